@@ -1,0 +1,153 @@
+"""FP64 CPU oracle for the SAND query path — TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The CUDA library never does, and this
+package never imports the library: they share no code, only the generated
+inputs of ``synth``.
+
+The arithmetic lives in ``sand_oracle.c`` (plain per-point double-precision
+loops, OpenMP over points); this module compiles it with gcc on first use
+(``-O2 -ffp-contract=off``, no fast-math) and marshals numpy arrays.
+Functions follow SAND (arxiv 2604.25936): ``lookup`` the octree of Sec. 3.2 /
+Eq. 7 with the level-of-detail clamp of Sec. 3.4, ``evaluate`` the T-MLP of
+Eq. 2 / Eq. 3 to given exit layers, ``query`` the whole inference procedure
+of Sec. 3.4, each optionally with the input gradient by reverse-mode chain
+rule.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sand_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle's shared library (gcc, OpenMP) if missing or stale."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fno-fast-math",
+                               "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            lib.oracle_lookup.argtypes = [ctypes.c_int, P, P, P, P, ctypes.c_int64, ctypes.c_int, P, P]
+            lib.oracle_eval.argtypes = [P, ctypes.c_double, P, P, ctypes.c_int64, P, ctypes.c_int, P, P, P]
+            lib.oracle_query.argtypes = [P, ctypes.c_double, P, ctypes.c_int, P, P, P, P, ctypes.c_int64,
+                                         ctypes.c_int, P, P, P]
+            lib.oracle_param_count.argtypes = [P]
+            lib.oracle_param_count.restype = ctypes.c_longlong
+            lib.oracle_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def threads() -> int:
+    """OpenMP threads the oracle runs on."""
+    return int(_load().oracle_threads())
+
+
+def _model_args(model):
+    hdr = np.ascontiguousarray(np.array(model.header_ints(), np.int32))
+    params = np.ascontiguousarray(model.flat(), np.float32)
+    n_expect = _load().oracle_param_count(_ptr(hdr))
+    if params.size != n_expect:
+        raise ValueError("parameter block has %d floats, header implies %d" % (params.size, n_expect))
+    return hdr, float(model.omega0), params
+
+
+def _pts(points):
+    p = np.ascontiguousarray(np.asarray(points, np.float32).reshape(-1, 3))
+    return p
+
+
+def lookup(octree, points, max_depth: int = 0):
+    """Exit layer (int32, -1 for NaN points) and stored far value (float64) per point."""
+    p = _pts(points)
+    n = p.shape[0]
+    d = np.empty(n, np.int32)
+    f = np.empty(n, np.float64)
+    child = np.ascontiguousarray(octree.child, np.int32)
+    dep = np.ascontiguousarray(octree.depth, np.uint8)
+    far = np.ascontiguousarray(octree.far, np.float32)
+    rc = _load().oracle_lookup(int(child.size), _ptr(child), _ptr(dep), _ptr(far), _ptr(p), n,
+                               int(max_depth), _ptr(d), _ptr(f))
+    if rc:
+        raise RuntimeError("oracle_lookup failed: %d" % rc)
+    return d, f
+
+
+def evaluate(model, points, depth, grad: bool = False, all_tails: bool = False):
+    """T-MLP outputs y_d at exit layer(s) `depth` (int or int array; <= 0 gives 0).
+
+    Returns y (float64 [n]); plus grad [n,3] if grad; plus ys [n,L] (y_1..y_d,
+    zero beyond d) if all_tails.
+    """
+    hdr, w0, params = _model_args(model)
+    p = _pts(points)
+    n = p.shape[0]
+    y = np.empty(n, np.float64)
+    g = np.empty((n, 3), np.float64) if grad else None
+    ys = np.empty((n, model.n_layers), np.float64) if all_tails else None
+    if np.isscalar(depth) or np.ndim(depth) == 0:
+        darr, cd = None, int(depth)
+    else:
+        darr, cd = np.ascontiguousarray(np.asarray(depth, np.int32)), 0
+    rc = _load().oracle_eval(_ptr(hdr), w0, _ptr(params), _ptr(p), n, _ptr(darr), cd, _ptr(y), _ptr(g), _ptr(ys))
+    if rc:
+        raise RuntimeError("oracle_eval failed: %d" % rc)
+    out = [y]
+    if grad:
+        out.append(g)
+    if all_tails:
+        out.append(ys)
+    return out[0] if len(out) == 1 else tuple(out)
+
+
+def query(model, octree, points, max_depth: int = 0, grad: bool = False, exit_layers: bool = False):
+    """SAND inference (Sec. 3.4): y per point (float64); optionally grad [n,3]
+    and exit layers (int32, -1 for NaN points)."""
+    hdr, w0, params = _model_args(model)
+    p = _pts(points)
+    n = p.shape[0]
+    y = np.empty(n, np.float64)
+    g = np.empty((n, 3), np.float64) if grad else None
+    d = np.empty(n, np.int32) if exit_layers else None
+    child = np.ascontiguousarray(octree.child, np.int32)
+    dep = np.ascontiguousarray(octree.depth, np.uint8)
+    far = np.ascontiguousarray(octree.far, np.float32)
+    rc = _load().oracle_query(_ptr(hdr), w0, _ptr(params), int(child.size), _ptr(child), _ptr(dep), _ptr(far),
+                              _ptr(p), n, int(max_depth), _ptr(y), _ptr(g), _ptr(d))
+    if rc:
+        raise RuntimeError("oracle_query failed: %d" % rc)
+    out = [y]
+    if grad:
+        out.append(g)
+    if exit_layers:
+        out.append(d)
+    return out[0] if len(out) == 1 else tuple(out)
+
+
+def full_depth(model, points, grad: bool = False):
+    """The plain T-MLP evaluated to its last layer at every point (no depth map)."""
+    return evaluate(model, points, model.n_layers, grad=grad)
