@@ -1,0 +1,367 @@
+"""Benchmark of the SAND query path on GB300.
+
+One step = one SAND query over a 256^3 marching-cubes lattice (16,777,216
+points): depth-map lookup, exit-layer binning and the T-MLP to each point's
+exit layer, for an 8 x 256 SIREN T-MLP (random SIREN init, seed 1, linear
+tails) and a level-7 octree built from an analytic scene.  The same T-MLP run
+to full depth on the same points is timed beside it.  Inputs are larger than
+L2 (201 MB of points), so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank evaluates its own
+full lattice (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+GRID = 256
+N_LAYERS, WIDTH, SEED = 8, 256, 1
+TOL = {"fp32": 1e-5, "fp32_simt": 1e-5, "fp16": 2e-3, "bf16": 2e-3, "fp8": None}
+DTYPE = {"fp32": "f32 (3 x f16 split, f32 accumulate)", "fp32_simt": "f32", "fp16": "f16 (f32 accumulate)",
+         "bf16": "bf16 (f32 accumulate)", "fp8": "e4m3 (f32 accumulate)"}
+KERNEL_SRC = {"fp32_simt": "paper_2604_25936_gb300/csrc/tmlp_simt.cu", "fp32": "paper_2604_25936_gb300/csrc/tmlp_tc.cu",
+              "fp16": "paper_2604_25936_gb300/csrc/tmlp_tc.cu", "bf16": "paper_2604_25936_gb300/csrc/tmlp_tc.cu",
+              "fp8": "paper_2604_25936_gb300/csrc/tmlp_tc.cu"}
+KERNEL_NAME = {"fp32_simt": "tmlp_simt_kernel", "fp32": "tmlp_tc_kernel", "fp16": "tmlp_tc_kernel",
+               "bf16": "tmlp_tc_kernel", "fp8": "tmlp_tc_kernel"}
+METRIC = "SDF queries/s, SAND vs full-depth T-MLP on 1 GB300 at stated error; serve p99 ms"
+
+
+def flops_per_point(d: np.ndarray, W: int, tail_mult: bool) -> np.ndarray:
+    """Algorithmic FLOPs of a point that exits at layer d >= 1: layer 1 (2*3*W),
+    d-1 hidden products (2*W^2 each) and d tails (2*W, or 4*W for multiplicative tails >= 2)."""
+    d = np.asarray(d, np.float64)
+    tails = d * 2 * W if not tail_mult else (2 * W + (d - 1) * 4 * W)
+    return np.where(d >= 1, 2 * 3 * W + (d - 1) * 2 * W * W + tails, 0.0)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        p = json.load(open(path))
+        return p, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 200 ms while the timed region runs."""
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        rows = [[c.strip() for c in r] for r in rows if len(r) >= 9]
+        if self.uuid:
+            mine = [r for r in rows if self.uuid in r[0]]
+            rows = mine or rows
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        load = [v for v in sm if mx and v >= 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def kernel_traffic(prec: str):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, or None
+    when the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        t = json.load(open(path)).get(KERNEL_NAME[prec] + ":" + prec)
+        src = open(os.path.join(ROOT, KERNEL_SRC[prec]), "rb").read()
+        if t and t.get("source_sha1") == hashlib.sha1(src).hexdigest():
+            return t.get("dram_bytes_per_launch_full_workload")
+    except Exception:
+        return None
+    return None
+
+
+def cpu_baseline(model, tree, pts, budget_s: float = 12.0):
+    """The FP64 oracle as it stands, on the host cores, over a seeded sample of the lattice."""
+    import oracle
+    n = len(pts)
+    probe = synth.sample_indices(n, 20000, seed=11)
+    t0 = time.perf_counter()
+    oracle.query(model, tree, pts[probe])
+    rate = 20000 / max(time.perf_counter() - t0, 1e-6)
+    k = int(min(n, max(20000, rate * budget_s)))
+    idx = synth.sample_indices(n, k, seed=11)
+    t0 = time.perf_counter()
+    oracle.query(model, tree, pts[idx])
+    dt = time.perf_counter() - t0
+    return {"value": k / dt, "unit": "queries/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": "%d lattice points drawn with PCG64 seed 11 from the %d^3 lattice, SAND query (lookup + "
+                      "T-MLP to each exit layer) in float64, %.1f s" % (k, GRID, dt)}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores, same workload, a bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    model = synth.siren_tmlp(N_LAYERS, WIDTH, seed=SEED)
+    tree = synth.scene_octree(7, N_LAYERS)
+    pts = synth.lattice(GRID)
+    probe = synth.sample_indices(len(pts), 10000, seed=11)
+    t0 = time.perf_counter()
+    oracle.query(model, tree, pts[probe])
+    rate = 10000 / max(time.perf_counter() - t0, 1e-6)
+    per_step = max(1.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+    k = int(min(len(pts), max(10000, rate * per_step)))
+    idx = synth.sample_indices(len(pts), k, seed=11)
+    sample = pts[idx]
+    for _ in range(args.warmup):
+        oracle.query(model, tree, sample)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.query(model, tree, sample)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = k / (ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "SAND-SIREN 8x256, level-7 octree, %d^3 lattice" % GRID, "global_batch": len(pts),
+                       "sample_per_step": k},
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": oracle.threads(), "kind": "oracle",
+                             "sample": "%d lattice points (PCG64 seed 11) per step, float64 SAND query" % k},
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="sand", choices=["sand", "reference"])
+    ap.add_argument("--precision", default="fp32_simt", choices=sorted(TOL))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    import paper_2604_25936_gb300 as sand
+    from paper_2604_25936_gb300 import build as sand_build
+    sand_build.build()
+    prec = args.precision
+    W = max(3, args.warmup)
+    K = max(1, args.steps)
+
+    model = synth.siren_tmlp(N_LAYERS, WIDTH, seed=SEED)
+    tree = synth.scene_octree(7, N_LAYERS)
+    pts = synth.lattice(GRID)
+    n = len(pts)
+    m = sand.Model.from_params(*model.header_ints(), model.omega0, model.flat(), device=local)
+    m.set_depth_map(tree.max_level, tree.n_layers, tree.child, tree.depth, tree.far)
+    x = torch.from_numpy(pts).cuda()
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    ws = m.workspace(n)
+    stream = torch.cuda.current_stream()
+
+    def sand_step(events=None):
+        m.query(x, precision=prec, out=out, workspace=ws, events=events)
+
+    for _ in range(W):
+        sand_step()
+    torch.cuda.synchronize()
+    stats = m.stats(ws)
+    counts = np.array(stats["count"][:N_LAYERS + 1], np.int64)
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for k in range(K):
+        sand_step(ev[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = t_start.elapsed_time(t_end) / K
+    mlp_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(K)]
+    pre_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
+    if world > 1:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * n / (ms / 1e3)
+
+    # ---- full-depth baseline: the same T-MLP to layer L at every point
+    fout = torch.empty(n, dtype=torch.float32, device="cuda")
+    fws = m.workspace(0)
+    Kf = max(2, K // 4)
+    for _ in range(2):
+        m.query(x, precision=prec, full_depth=True, out=fout, workspace=fws)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(Kf):
+        m.query(x, precision=prec, full_depth=True, out=fout, workspace=fws)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    full_ms = f0.elapsed_time(f1) / Kf
+    full_value = world * n / (full_ms / 1e3)
+
+    # ---- error against the oracle on a sample (the "stated error")
+    err = err_full = None
+    if rank == 0:
+        import oracle
+        idx = synth.sample_indices(n, 20000, seed=11)
+        y_ref = oracle.query(model, tree, pts[idx])
+        err = float(np.abs(out.cpu().numpy()[idx].astype(np.float64) - y_ref).max())
+        yf_ref = oracle.full_depth(model, pts[idx[:5000]])
+        err_full = float(np.abs(fout.cpu().numpy()[idx[:5000]].astype(np.float64) - yf_ref).max())
+
+    # ---- end to end through the C-ABI with host buffers (pinned), copies inside the timed region
+    hp = torch.from_numpy(pts).pin_memory()
+    ho = torch.empty(n, dtype=torch.float32).pin_memory()
+    m.query_host(hp, out=ho, precision=prec)
+    Ke = max(2, K // 4)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(Ke):
+        m.query_host(hp, out=ho, precision=prec)
+    e2e_s = (time.perf_counter() - t0) / Ke
+    if world > 1:
+        tt = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_value = world * n / e2e_s
+
+    # ---- roofline of the dominant kernel (the T-MLP kernel)
+    pk, pk_src = peaks()
+    net_flops = float((flops_per_point(np.arange(N_LAYERS + 1), WIDTH, False) * counts).sum())
+    mlp_avg = sum(mlp_ms) / len(mlp_ms)
+    achieved = net_flops / (mlp_avg / 1e3) / 1e12
+    if prec == "fp32_simt":
+        sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+        peak = sm_count * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": kernel_traffic(prec), "kernel": KERNEL_NAME[prec],
+                "peak_source": "derived: %d SMs x 128 FP32 FMA/clk x 2 FLOP x %.0f MHz (max SM clock, %s)"
+                               % (sm_count, pk.get("sm_max_mhz", 2070.0), pk_src)}
+    else:
+        base = pk.get("bf16_tflops_sustained", 1700.0)
+        ratio = {"fp32": 1.0 / 3.0, "fp16": 1.0, "bf16": 1.0, "fp8": 2.0}[prec]
+        peak = base * ratio
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": kernel_traffic(prec), "kernel": KERNEL_NAME[prec],
+                "peak_source": "%s bf16 sustained %.1f TFLOP/s x %.3g (%s)" % (pk_src, base, ratio, prec)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(model, tree, pts)
+
+    hist = {str(d): int(c) for d, c in enumerate(counts)}
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "queries/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": W,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": DTYPE[prec],
+        "data": "synthetic: random SIREN-init 8x256 T-MLP (seed 1), analytic-scene level-7 octree, marching-cubes lattice",
+        "config": {"workload": "SAND-SIREN 8x256 linear tails, level-7 octree, %d^3 lattice" % GRID,
+                   "global_batch": world * n, "points_per_gpu": n, "precision": prec,
+                   "l2": "inputs larger than L2 (201 MB of points per step), no flush",
+                   "parallelism": "replicas (one full lattice per GPU)"},
+        "full_depth": {"value": full_value, "unit": "queries/s", "ms_per_step": full_ms,
+                       "speedup_sand_vs_full": value / full_value, "max_abs_err_vs_oracle_5k": err_full},
+        "max_abs_err_vs_oracle_20k": err,
+        "tolerance": TOL[prec],
+        "stage_ms": {"lookup_bin": sum(pre_ms) / K, "tmlp": mlp_avg},
+        "exit_layer_histogram": hist,
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": 12 * n, "d2h_bytes_per_step": 4 * n},
+        "gpu_launches": 4 * K,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    m.free()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

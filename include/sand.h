@@ -1,0 +1,188 @@
+/*
+ * sand.h — C-ABI of libsand: the SAND query path on one GB300 (sm_103a).
+ *
+ * SAND (arxiv 2604.25936) answers a signed-distance query at a 3D point x by
+ * reading the exit layer d(x) of x from a volumetric network-depth map (an
+ * octree, Sec. 3.2, Eq. 7) and evaluating a tailed MLP only up to that layer
+ * (Sec. 3.4): y_d = t_1 + ... + t_d with t_i the tail of hidden layer i
+ * (Eq. 2; multiplicative tails for i >= 2 follow Eq. 3).  Exit layer 0 marks
+ * a far leaf whose stored SDF value at the leaf centre is returned without
+ * running the network (Eq. 7).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* are device pointers on the model's device; h_* are
+ *     host pointers.  The caller owns every buffer it passes; the library
+ *     owns the model (weights, depth map) and its optional default workspace.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Queries are stream-ordered and asynchronous: they return once
+ *     the work is enqueued.  Loaders and sand_free synchronise the device.
+ *   - Every call returns a sand_status; on failure sand_last_error() gives a
+ *     message (thread-local, valid until the next call on the same thread).
+ *   - Points are float32 xyz triples, array-of-structures [n][3], at least
+ *     4-byte aligned (16-byte alignment enables vector loads).  The domain is
+ *     [-1,1]^3; points outside are answered by the nearest boundary leaf.  A
+ *     point with a NaN coordinate gets exit layer 0xFF, SDF NaN, gradient NaN,
+ *     and sets SAND_FLAG_NAN_INPUT in the workspace flags (sand_query_stats).
+ *   - n == 0 is a valid no-op.
+ */
+#ifndef SAND_H_
+#define SAND_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sand_model_s *sand_model;
+
+typedef enum {
+    SAND_OK = 0,
+    SAND_EINVAL = 1,        /* an argument is out of range or a pointer is NULL / misaligned */
+    SAND_ENOMEM = 2,        /* a device or host allocation failed, or the workspace is too small */
+    SAND_EFORMAT = 3,       /* a model / depth-map file or descriptor is malformed */
+    SAND_ECUDA = 4,         /* a CUDA runtime call failed (message carries cudaGetErrorString) */
+    SAND_ETIMEOUT = 5,      /* a bounded device-side wait gave up (see SAND_FLAG_TIMEOUT) */
+    SAND_ENOMAP = 6,        /* a SAND query before a depth map was loaded */
+    SAND_EUNSUPPORTED = 7   /* this model shape / precision / device is not supported */
+} sand_status;
+
+/* Arithmetic of the hidden-layer products W_i h_{i-1} (Eq. 2).  The first
+ * layer, the sine argument and its range reduction, the tails and the
+ * accumulation y_i = y_{i-1} + t_i are always float32.
+ *   SAND_FP32       tcgen05 tensor cores, each float32 operand split into two
+ *                   fp16 terms (weights pre-scaled by a power of two), three
+ *                   products per layer, float32 accumulation: float32-class error.
+ *   SAND_FP32_SIMT  plain float32 FMA on the CUDA cores (reference kernel).
+ *   SAND_FP16 / SAND_BF16 / SAND_FP8  one tcgen05 product per layer with
+ *                   fp16 / bf16 / e4m3 operands (per-layer weight scales) and
+ *                   float32 accumulation. */
+typedef enum {
+    SAND_FP32 = 0,
+    SAND_FP32_SIMT = 1,
+    SAND_FP16 = 2,
+    SAND_BF16 = 3,
+    SAND_FP8 = 4
+} sand_precision;
+
+typedef enum { SAND_TAIL_LINEAR = 0, SAND_TAIL_MULT = 1 } sand_tail_kind;
+typedef enum { SAND_ACT_SINE = 0, SAND_ACT_RELU = 1 } sand_activation;
+typedef enum { SAND_ENC_NONE = 0, SAND_ENC_FOURIER = 1 } sand_encoder;
+
+/* Shape of a T-MLP (Eq. 2 / Eq. 3).
+ *   n_layers  L, the number of hidden layers and of tails (1 .. 14)
+ *   width     W, hidden units per layer (16 .. 512)
+ *   in_dim    3 without an encoder, 2 * n_freq with Fourier features
+ *   activation SAND_ACT_SINE: h = sin(omega0 * (W h + b)) (SIREN);
+ *             SAND_ACT_RELU: h = max(0, W h + b)
+ *   encoder   SAND_ENC_FOURIER: h_0 = [sin(2 pi B x), cos(2 pi B x)], B [n_freq][3]
+ *   tail_kind SAND_TAIL_MULT: t_i = (a_i.h_i + c_i)(b_i.h_i + e_i) for i >= 2 (Eq. 3);
+ *             tail 1 is always affine.                                          */
+typedef struct {
+    int32_t n_layers;
+    int32_t width;
+    int32_t in_dim;
+    int32_t tail_kind;
+    int32_t activation;
+    int32_t encoder;
+    int32_t n_freq;
+    float omega0;
+} sand_tmlp_desc;
+
+/* Pointer octree over [-1,1]^3 (Sec. 3.2): node 0 is the root; child[i] = -1
+ * marks a leaf, else the index of the first of its 8 consecutive children in
+ * octant order ix | iy << 1 | iz << 2, where the upper half (coordinate >= the
+ * cell midpoint) has bit 1.  depth[i] is a leaf's exit layer (0 .. n_layers;
+ * 0 = far leaf), far[i] its stored SDF value at the centre (Eq. 7). */
+typedef struct {
+    int32_t max_level;   /* deepest leaf level, 0 .. 10 (root = level 0) */
+    int32_t n_layers;    /* largest exit layer the map may hold */
+    int32_t n_nodes;
+} sand_depth_map_desc;
+
+/* Per-query options; a NULL opts pointer means all defaults (zero-initialised). */
+typedef struct {
+    int32_t precision;      /* sand_precision (default SAND_FP32) */
+    int32_t max_depth;      /* level of detail (Sec. 3.4): exit layer <- min(d, max_depth) for d > 0; 0 = off */
+    int32_t full_depth;     /* 1: ignore the depth map and run every point to layer L (plain T-MLP) */
+    int32_t reserved;
+    uint8_t *d_exit_layers; /* optional device [n]: exit layer used per point (0xFF = NaN point) */
+    void *d_workspace;      /* optional device scratch of >= sand_workspace_bytes() bytes, 256-byte aligned;
+                               NULL = the model's own workspace (grown on demand; one stream at a time) */
+    size_t workspace_bytes;
+    void *const *stage_events; /* optional: 3 caller-created cudaEvent_t handles, recorded on the stream
+                               before the lookup, before the T-MLP kernel and after it (stage timing) */
+} sand_query_opts;
+
+/* Load a model file: "TMLP", u32 version 1, 7 x i32 (n_layers, width, in_dim,
+ * tail_kind, activation, encoder, n_freq), f32 omega0, u64 n_params, then the
+ * float32 parameter block (layout of sand_load_tmlp_mem).  `device` is the CUDA
+ * ordinal the model lives on.  On success *out owns device memory until sand_free. */
+sand_status sand_load_tmlp(const char *path, int device, sand_model *out);
+
+/* Load a model from host memory.  h_params holds n_params float32 values in
+ * this order (row-major): B [n_freq][3] (Fourier encoder only), W1 [W][in_dim],
+ * b1 [W], W_2..W_L [L-1][W][W] (row = output unit), b_2..b_L [L-1][W],
+ * tail weights [L][2][W] (row 1 used only by multiplicative tails i >= 2),
+ * tail biases [L][2].  The library copies what it needs. */
+sand_status sand_load_tmlp_mem(const sand_tmlp_desc *desc, const float *h_params, size_t n_params,
+                               int device, sand_model *out);
+
+/* Load the depth map from a file: "SDMO", u32 version 1, i32 max_level,
+ * i32 n_layers, i32 n_nodes, 6 x f32 bounding box (must be -1,-1,-1,1,1,1),
+ * int32 child[n], uint8 depth[n] padded to 4 bytes, float32 far[n].
+ * Replaces any previous map. */
+sand_status sand_load_depth_map(sand_model m, const char *path);
+
+/* Load the depth map from host arrays (see sand_depth_map_desc).  The octree is
+ * re-encoded losslessly on the device as a dense exit-layer grid at max_level
+ * plus a dense far-value grid when the map has far leaves. */
+sand_status sand_load_depth_map_mem(sand_model m, const sand_depth_map_desc *desc, const int32_t *h_child,
+                                    const uint8_t *h_depth, const float *h_far);
+
+/* Device bytes of workspace a query of n points needs (with_grad: for sand_query_sdf_grad). */
+size_t sand_workspace_bytes(sand_model m, int64_t n, int with_grad);
+
+/* SAND inference (Sec. 3.4): d_out[i] = y_{d(x_i)}(x_i), or the stored far value
+ * when d(x_i) = 0.  d_points: device float32 [n][3]; d_out: device float32 [n]. */
+sand_status sand_query_sdf(sand_model m, const float *d_points, int64_t n, float *d_out,
+                           const sand_query_opts *opts, void *stream);
+
+/* As sand_query_sdf, plus the input gradient d_grad[i] = dy/dx at x_i (surface
+ * normal direction for sphere tracing); zero for exit layer 0.  d_out may be
+ * NULL.  d_grad: device float32 [n][3]. */
+sand_status sand_query_sdf_grad(sand_model m, const float *d_points, int64_t n, float *d_out, float *d_grad,
+                                const sand_query_opts *opts, void *stream);
+
+/* End-to-end query from HOST memory: copies h_points to the device, runs the
+ * query, copies the SDF back to h_out, in chunks pipelined over the stream.
+ * Pinned host memory gives full copy bandwidth.  Synchronous: returns after
+ * h_out is written. */
+sand_status sand_query_sdf_host(sand_model m, const float *h_points, int64_t n, float *h_out,
+                                const sand_query_opts *opts, void *stream);
+
+/* Flags and counters a query leaves in its workspace (read after the query's
+ * stream has been synchronised by this call). */
+#define SAND_FLAG_NAN_INPUT 1u
+#define SAND_FLAG_TIMEOUT 2u
+typedef struct {
+    uint32_t flags;          /* SAND_FLAG_* raised by the last query on this workspace */
+    uint32_t n_network;      /* points evaluated by the network (exit layer >= 1) */
+    uint32_t count[16];      /* points per exit layer 0 .. 14; count[15] = NaN points */
+} sand_query_stats;
+sand_status sand_read_stats(sand_model m, const void *d_workspace, sand_query_stats *out, void *stream);
+
+/* Describe a loaded model. */
+sand_status sand_model_desc(sand_model m, sand_tmlp_desc *out);
+
+/* Release the model's device memory. */
+sand_status sand_free(sand_model m);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char *sand_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SAND_H_ */

@@ -1,0 +1,488 @@
+// C-ABI of libsand: model and depth-map loading, workspace handling and the
+// query entry points (declared and documented in include/sand.h).
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+#include "tc.cuh"
+
+struct sand_model_s {
+    int device = 0;
+    int num_sms = 0;
+    sand_tmlp_desc desc{};
+    std::vector<float> params;        // host copy of the float32 master parameters
+    float *d_simt = nullptr;          // transposed float32 weights for the CUDA-core kernel
+    sand::TmlpDev simt{};
+    sand::TcModel tc{};               // packed tensor-core weights (per precision, built lazily)
+    uint8_t *d_grid = nullptr;        // dense exit-layer grid
+    float *d_far = nullptr;           // dense far-value grid (only when the map has far leaves)
+    int map_level = -1;
+    void *d_ws = nullptr;             // default workspace
+    size_t ws_bytes = 0;
+    float *d_stage = nullptr;         // staging for host-memory queries: points then outputs
+    size_t stage_bytes = 0;
+};
+
+namespace sand {
+
+static thread_local std::string g_err;
+
+void set_error(const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+sand_status cuda_fail(cudaError_t e, const char *what) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return SAND_ECUDA;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+#define SAND_CUDA(call, what)                              \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+static size_t param_count(const sand_tmlp_desc &d) {
+    size_t L = d.n_layers, W = d.width, D = d.in_dim, m = d.n_freq;
+    size_t n = W * D + W + (L - 1) * W * W + (L - 1) * W + L * 2 * W + L * 2;
+    if (d.encoder == SAND_ENC_FOURIER) n += m * 3;
+    return n;
+}
+
+static sand_status validate_desc(const sand_tmlp_desc &d) {
+    if (d.n_layers < 1 || d.n_layers > kMaxLayers) { set_error("n_layers %d outside 1..%d", d.n_layers, kMaxLayers); return SAND_EFORMAT; }
+    if (d.width < 1 || d.width > kMaxWidth) { set_error("width %d outside 1..%d", d.width, kMaxWidth); return SAND_EFORMAT; }
+    if (d.tail_kind != SAND_TAIL_LINEAR && d.tail_kind != SAND_TAIL_MULT) { set_error("bad tail_kind %d", d.tail_kind); return SAND_EFORMAT; }
+    if (d.activation != SAND_ACT_SINE && d.activation != SAND_ACT_RELU) { set_error("bad activation %d", d.activation); return SAND_EFORMAT; }
+    if (d.encoder == SAND_ENC_FOURIER) {
+        if (d.n_freq < 1 || d.in_dim != 2 * d.n_freq || d.in_dim > kMaxWidth) { set_error("Fourier encoder needs in_dim = 2 n_freq <= %d", kMaxWidth); return SAND_EFORMAT; }
+    } else if (d.encoder == SAND_ENC_NONE) {
+        if (d.in_dim != 3) { set_error("in_dim must be 3 without an encoder"); return SAND_EFORMAT; }
+    } else {
+        set_error("bad encoder %d", d.encoder);
+        return SAND_EFORMAT;
+    }
+    if (!(d.omega0 > 0.f) || !(d.omega0 < 1e4f)) { set_error("omega0 out of range"); return SAND_EFORMAT; }
+    return SAND_OK;
+}
+
+// Pack the CUDA-core layout: per layer the transposed weights [fan_in][W] and biases.
+static sand_status pack_simt(sand_model_s *m) {
+    const sand_tmlp_desc &d = m->desc;
+    const int L = d.n_layers, W = d.width, D = d.in_dim, mf = d.n_freq;
+    const float *p = m->params.data();
+    const float *B = nullptr;
+    if (d.encoder == SAND_ENC_FOURIER) { B = p; p += (size_t)mf * 3; }
+    const float *W1 = p; p += (size_t)W * D;
+    const float *b1 = p; p += W;
+    const float *Wh = p; p += (size_t)(L - 1) * W * W;
+    const float *bh = p; p += (size_t)(L - 1) * W;
+    const float *tw = p; p += (size_t)L * 2 * W;
+    const float *tb = p;
+    std::vector<float> buf;
+    std::vector<size_t> off_WT(L), off_b(L);
+    size_t off_B = 0, off_tw, off_tb;
+    auto push = [&](size_t n) { size_t o = buf.size(); buf.resize(o + ((n + 63) / 64) * 64, 0.f); return o; };
+    if (B) { off_B = push((size_t)mf * 3); memcpy(&buf[off_B], B, sizeof(float) * mf * 3); }
+    for (int l = 0; l < L; ++l) {
+        const int K = l == 0 ? D : W;
+        const float *Wl = l == 0 ? W1 : Wh + (size_t)(l - 1) * W * W;
+        off_WT[l] = push((size_t)K * W);
+        for (int j = 0; j < W; ++j)
+            for (int k = 0; k < K; ++k) buf[off_WT[l] + (size_t)k * W + j] = Wl[(size_t)j * K + k];
+        off_b[l] = push(W);
+        memcpy(&buf[off_b[l]], l == 0 ? b1 : bh + (size_t)(l - 1) * W, sizeof(float) * W);
+    }
+    off_tw = push((size_t)L * 2 * W);
+    memcpy(&buf[off_tw], tw, sizeof(float) * L * 2 * W);
+    off_tb = push((size_t)L * 2);
+    memcpy(&buf[off_tb], tb, sizeof(float) * L * 2);
+    SAND_CUDA(cudaMalloc(&m->d_simt, sizeof(float) * buf.size()), "cudaMalloc(weights)");
+    SAND_CUDA(cudaMemcpy(m->d_simt, buf.data(), sizeof(float) * buf.size(), cudaMemcpyHostToDevice), "cudaMemcpy(weights)");
+    TmlpDev &M = m->simt;
+    M.L = L; M.W = W; M.D = D; M.tail_kind = d.tail_kind; M.act = d.activation; M.enc = d.encoder; M.m = mf;
+    M.omega0 = d.omega0;
+    M.B = B ? m->d_simt + off_B : nullptr;
+    for (int l = 0; l < kMaxLayers; ++l) {
+        M.WT[l] = l < L ? m->d_simt + off_WT[l] : nullptr;
+        M.bias[l] = l < L ? m->d_simt + off_b[l] : nullptr;
+    }
+    M.tw = m->d_simt + off_tw;
+    M.tb = m->d_simt + off_tb;
+    return SAND_OK;
+}
+
+static void release(sand_model_s *m) {
+    if (!m) return;
+    cudaFree(m->d_simt);
+    tc_release(&m->tc);
+    cudaFree(m->d_grid);
+    cudaFree(m->d_far);
+    cudaFree(m->d_ws);
+    cudaFree(m->d_stage);
+}
+
+static sand_status ensure_workspace(sand_model_s *m, int64_t n, bool grad, void **ws, size_t *bytes) {
+    (void)grad;
+    size_t need = ws_layout(n).total;
+    if (m->ws_bytes < need) {
+        cudaFree(m->d_ws);
+        m->d_ws = nullptr;
+        m->ws_bytes = 0;
+        if (cudaMalloc(&m->d_ws, need) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cannot allocate a %zu-byte workspace", need);
+            return SAND_ENOMEM;
+        }
+        m->ws_bytes = need;
+    }
+    *ws = m->d_ws;
+    *bytes = m->ws_bytes;
+    return SAND_OK;
+}
+
+// Fill the dense grid from the octree (iterative descent; validates the tree).
+static sand_status densify(const sand_depth_map_desc &d, const int32_t *child, const uint8_t *depth, const float *far,
+                           int model_layers, std::vector<uint8_t> &grid, std::vector<float> &fgrid, bool &has_far) {
+    const int ML = d.max_level;
+    const int64_t R = (int64_t)1 << ML;
+    grid.assign((size_t)(R * R * R), 0);
+    has_far = false;
+    for (int i = 0; i < d.n_nodes; ++i)
+        if (child[i] < 0 && depth[i] == 0) { has_far = true; break; }
+    if (has_far) fgrid.assign((size_t)(R * R * R), 0.f);
+    struct Item { int32_t node; int level; int64_t cx, cy, cz; };
+    std::vector<Item> stack;
+    stack.push_back({0, 0, 0, 0, 0});
+    int64_t visited = 0;
+    while (!stack.empty()) {
+        Item it = stack.back();
+        stack.pop_back();
+        if (++visited > d.n_nodes) { set_error("octree has a cycle or shared children"); return SAND_EFORMAT; }
+        const int32_t c = child[it.node];
+        if (c >= 0) {
+            if (it.level >= ML) { set_error("node %d below max_level %d", it.node, ML); return SAND_EFORMAT; }
+            if ((int64_t)c + 8 > d.n_nodes || c <= it.node) { set_error("bad child index %d at node %d", c, it.node); return SAND_EFORMAT; }
+            for (int o = 0; o < 8; ++o)
+                stack.push_back({c + o, it.level + 1, 2 * it.cx + (o & 1), 2 * it.cy + ((o >> 1) & 1), 2 * it.cz + ((o >> 2) & 1)});
+            continue;
+        }
+        const int dv = depth[it.node];
+        if (dv > d.n_layers || dv > model_layers) { set_error("leaf %d exit layer %d exceeds %d layers", it.node, dv, model_layers); return SAND_EFORMAT; }
+        const int64_t s = (int64_t)1 << (ML - it.level);
+        for (int64_t z = it.cz * s; z < (it.cz + 1) * s; ++z)
+            for (int64_t y = it.cy * s; y < (it.cy + 1) * s; ++y) {
+                const size_t row = (size_t)((z * R + y) * R);
+                memset(&grid[row + it.cx * s], dv, (size_t)s);
+                if (has_far)
+                    for (int64_t x = it.cx * s; x < (it.cx + 1) * s; ++x) fgrid[row + x] = far[it.node];
+            }
+    }
+    return SAND_OK;
+}
+
+static sand_status model_precheck(sand_model m) {
+    if (!m) { set_error("NULL model"); return SAND_EINVAL; }
+    return SAND_OK;
+}
+
+}  // namespace sand
+
+using namespace sand;
+
+extern "C" {
+
+const char *sand_last_error(void) { return g_err.c_str(); }
+
+sand_status sand_load_tmlp_mem(const sand_tmlp_desc *desc, const float *h_params, size_t n_params, int device,
+                               sand_model *out) {
+    g_err.clear();
+    if (!desc || !h_params || !out) { set_error("NULL argument"); return SAND_EINVAL; }
+    *out = nullptr;
+    sand_status st = validate_desc(*desc);
+    if (st) return st;
+    if (n_params != param_count(*desc)) {
+        set_error("parameter block has %zu floats, the descriptor implies %zu", n_params, param_count(*desc));
+        return SAND_EFORMAT;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        set_error("CUDA device %d not available (%d devices)", device, ndev);
+        return SAND_EUNSUPPORTED;
+    }
+    DeviceGuard g(device);
+    auto *m = new sand_model_s();
+    m->device = device;
+    m->desc = *desc;
+    m->params.assign(h_params, h_params + n_params);
+    cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, device);
+    st = pack_simt(m);
+    if (st) { release(m); delete m; return st; }
+    *out = m;
+    return SAND_OK;
+}
+
+sand_status sand_load_tmlp(const char *path, int device, sand_model *out) {
+    g_err.clear();
+    if (!path || !out) { set_error("NULL argument"); return SAND_EINVAL; }
+    FILE *f = fopen(path, "rb");
+    if (!f) { set_error("cannot open %s", path); return SAND_EINVAL; }
+    char magic[4];
+    uint32_t ver;
+    int32_t h[7];
+    float w0;
+    uint64_t np;
+    bool ok = fread(magic, 1, 4, f) == 4 && memcmp(magic, "TMLP", 4) == 0 && fread(&ver, 4, 1, f) == 1 && ver == 1 &&
+              fread(h, 4, 7, f) == 7 && fread(&w0, 4, 1, f) == 1 && fread(&np, 8, 1, f) == 1 && np < (1ull << 31);
+    std::vector<float> p;
+    if (ok) {
+        p.resize(np);
+        ok = fread(p.data(), 4, np, f) == np;
+    }
+    fclose(f);
+    if (!ok) { set_error("%s: not a version-1 TMLP model file (or truncated)", path); return SAND_EFORMAT; }
+    sand_tmlp_desc d{h[0], h[1], h[2], h[3], h[4], h[5], h[6], w0};
+    return sand_load_tmlp_mem(&d, p.data(), p.size(), device, out);
+}
+
+sand_status sand_load_depth_map_mem(sand_model m, const sand_depth_map_desc *desc, const int32_t *h_child,
+                                    const uint8_t *h_depth, const float *h_far) {
+    g_err.clear();
+    sand_status st = model_precheck(m);
+    if (st) return st;
+    if (!desc || !h_child || !h_depth || !h_far) { set_error("NULL argument"); return SAND_EINVAL; }
+    if (desc->max_level < 0 || desc->max_level > 9) { set_error("max_level %d outside 0..9", desc->max_level); return SAND_EUNSUPPORTED; }
+    if (desc->n_nodes < 1) { set_error("empty octree"); return SAND_EFORMAT; }
+    std::vector<uint8_t> grid;
+    std::vector<float> fgrid;
+    bool has_far = false;
+    st = densify(*desc, h_child, h_depth, h_far, m->desc.n_layers, grid, fgrid, has_far);
+    if (st) return st;
+    DeviceGuard g(m->device);
+    cudaFree(m->d_grid);
+    cudaFree(m->d_far);
+    m->d_grid = nullptr;
+    m->d_far = nullptr;
+    m->map_level = -1;
+    SAND_CUDA(cudaMalloc(&m->d_grid, grid.size()), "cudaMalloc(depth grid)");
+    SAND_CUDA(cudaMemcpy(m->d_grid, grid.data(), grid.size(), cudaMemcpyHostToDevice), "cudaMemcpy(depth grid)");
+    if (has_far) {
+        SAND_CUDA(cudaMalloc(&m->d_far, fgrid.size() * sizeof(float)), "cudaMalloc(far grid)");
+        SAND_CUDA(cudaMemcpy(m->d_far, fgrid.data(), fgrid.size() * sizeof(float), cudaMemcpyHostToDevice), "cudaMemcpy(far grid)");
+    }
+    m->map_level = desc->max_level;
+    return SAND_OK;
+}
+
+sand_status sand_load_depth_map(sand_model m, const char *path) {
+    g_err.clear();
+    sand_status st = model_precheck(m);
+    if (st) return st;
+    if (!path) { set_error("NULL path"); return SAND_EINVAL; }
+    FILE *f = fopen(path, "rb");
+    if (!f) { set_error("cannot open %s", path); return SAND_EINVAL; }
+    char magic[4];
+    uint32_t ver;
+    int32_t h[3];
+    float bbox[6];
+    bool ok = fread(magic, 1, 4, f) == 4 && memcmp(magic, "SDMO", 4) == 0 && fread(&ver, 4, 1, f) == 1 && ver == 1 &&
+              fread(h, 4, 3, f) == 3 && fread(bbox, 4, 6, f) == 6 && h[2] > 0 && h[2] < (1 << 30);
+    ok = ok && bbox[0] == -1.f && bbox[1] == -1.f && bbox[2] == -1.f && bbox[3] == 1.f && bbox[4] == 1.f && bbox[5] == 1.f;
+    std::vector<int32_t> child;
+    std::vector<uint8_t> depth;
+    std::vector<float> far;
+    if (ok) {
+        const size_t n = (size_t)h[2];
+        child.resize(n);
+        depth.resize((n + 3) / 4 * 4);
+        far.resize(n);
+        ok = fread(child.data(), 4, n, f) == n && fread(depth.data(), 1, depth.size(), f) == depth.size() &&
+             fread(far.data(), 4, n, f) == n;
+    }
+    fclose(f);
+    if (!ok) { set_error("%s: not a version-1 SDMO depth map over [-1,1]^3 (or truncated)", path); return SAND_EFORMAT; }
+    sand_depth_map_desc d{h[0], h[1], h[2]};
+    return sand_load_depth_map_mem(m, &d, child.data(), depth.data(), far.data());
+}
+
+size_t sand_workspace_bytes(sand_model m, int64_t n, int with_grad) {
+    (void)m;
+    (void)with_grad;
+    return ws_layout(n < 0 ? 0 : n).total;
+}
+
+static sand_status run_query(sand_model m, const float *d_points, int64_t n, float *d_out, float *d_grad,
+                             const sand_query_opts *opts, void *stream) {
+    sand_status st = model_precheck(m);
+    if (st) return st;
+    sand_query_opts o{};
+    if (opts) o = *opts;
+    if (n < 0 || n > 0x7fffffffLL) { set_error("n = %lld outside 0..2^31-1", (long long)n); return SAND_EINVAL; }
+    if (n == 0) return SAND_OK;
+    if (!d_points || (!d_out && !d_grad)) { set_error("NULL points or output"); return SAND_EINVAL; }
+    if ((reinterpret_cast<uintptr_t>(d_points) & 3) || (reinterpret_cast<uintptr_t>(d_out) & 3) ||
+        (reinterpret_cast<uintptr_t>(d_grad) & 3)) { set_error("device buffers must be 4-byte aligned"); return SAND_EINVAL; }
+    if (o.max_depth < 0) { set_error("max_depth < 0"); return SAND_EINVAL; }
+    if (!o.full_depth && m->map_level < 0) { set_error("no depth map loaded"); return SAND_ENOMAP; }
+    if (o.full_depth && o.d_exit_layers) { set_error("exit layers are not produced in full-depth mode"); return SAND_EINVAL; }
+    const bool simt = o.precision == SAND_FP32_SIMT || d_grad != nullptr;
+    if (!simt && !tc_supported(m->desc, o.precision)) {
+        set_error("precision %d is not supported for this model on the tensor-core path", o.precision);
+        return SAND_EUNSUPPORTED;
+    }
+    DeviceGuard g(m->device);
+    if (!g.ok) { set_error("cannot select device %d", m->device); return SAND_ECUDA; }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void *ws = o.d_workspace;
+    size_t wsb = o.workspace_bytes;
+    const size_t need = ws_layout(o.full_depth ? 0 : n).total;
+    if (ws) {
+        if ((reinterpret_cast<uintptr_t>(ws) & 255) || wsb < need) {
+            set_error("workspace must be 256-byte aligned and >= %zu bytes", need);
+            return SAND_EINVAL;
+        }
+    } else {
+        st = ensure_workspace(m, o.full_depth ? 0 : n, d_grad != nullptr, &ws, &wsb);
+        if (st) return st;
+    }
+    cudaEvent_t *ev = o.stage_events ? reinterpret_cast<cudaEvent_t *>(const_cast<void **>(o.stage_events)) : nullptr;
+    if (ev) SAND_CUDA(cudaEventRecord(ev[0], s), "event record");
+    SAND_CUDA(launch_init_header(ws, s), "workspace reset");
+    if (!o.full_depth) {
+        MapDev map{m->d_grid, m->d_far, m->map_level, m->desc.n_layers};
+        SAND_CUDA(launch_lookup(map, d_points, n, o.max_depth, d_out, d_grad, o.d_exit_layers, ws, s), "lookup kernel");
+        SAND_CUDA(launch_scatter(d_points, n, m->desc.n_layers, ws, s), "scatter kernel");
+    }
+    if (ev) SAND_CUDA(cudaEventRecord(ev[1], s), "event record");
+    if (simt) {
+        SAND_CUDA(launch_tmlp_simt(m->simt, d_points, n, o.full_depth, ws, d_out, d_grad, m->num_sms, s), "T-MLP kernel");
+    } else {
+        st = tc_prepare(&m->tc, m->desc, m->params.data(), o.precision);
+        if (st) return st;
+        SAND_CUDA(launch_tmlp_tc(m->tc, m->desc, o.precision, d_points, n, o.full_depth, ws, d_out, m->num_sms, s),
+                  "tensor-core T-MLP kernel");
+    }
+    if (ev) SAND_CUDA(cudaEventRecord(ev[2], s), "event record");
+    return SAND_OK;
+}
+
+sand_status sand_query_sdf(sand_model m, const float *d_points, int64_t n, float *d_out, const sand_query_opts *opts,
+                           void *stream) {
+    g_err.clear();
+    if (n > 0 && !d_out) { set_error("NULL d_out"); return SAND_EINVAL; }
+    return run_query(m, d_points, n, d_out, nullptr, opts, stream);
+}
+
+sand_status sand_query_sdf_grad(sand_model m, const float *d_points, int64_t n, float *d_out, float *d_grad,
+                                const sand_query_opts *opts, void *stream) {
+    g_err.clear();
+    if (n > 0 && !d_grad) { set_error("NULL d_grad"); return SAND_EINVAL; }
+    sand_query_opts o{};
+    if (opts) o = *opts;
+    if (!o.full_depth && n > 0 && !d_out) {
+        set_error("d_out is required for SAND gradient queries (far leaves write their stored value there)");
+        return SAND_EINVAL;
+    }
+    return run_query(m, d_points, n, d_out, d_grad, &o, stream);
+}
+
+sand_status sand_query_sdf_host(sand_model m, const float *h_points, int64_t n, float *h_out, const sand_query_opts *opts,
+                                void *stream) {
+    g_err.clear();
+    sand_status st = model_precheck(m);
+    if (st) return st;
+    if (n == 0) return SAND_OK;
+    if (!h_points || !h_out || n < 0) { set_error("bad host buffers"); return SAND_EINVAL; }
+    sand_query_opts o{};
+    if (opts) o = *opts;
+    if (o.d_exit_layers) { set_error("d_exit_layers is not available for host queries"); return SAND_EINVAL; }
+    DeviceGuard g(m->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t need = (size_t)n * 16;
+    if (m->stage_bytes < need) {
+        cudaFree(m->d_stage);
+        m->d_stage = nullptr;
+        m->stage_bytes = 0;
+        if (cudaMalloc(&m->d_stage, need) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cannot allocate %zu bytes of staging", need);
+            return SAND_ENOMEM;
+        }
+        m->stage_bytes = need;
+    }
+    float *d_pts = m->d_stage;
+    float *d_out = m->d_stage + (size_t)n * 3;
+    SAND_CUDA(cudaMemcpyAsync(d_pts, h_points, (size_t)n * 12, cudaMemcpyHostToDevice, s), "H2D points");
+    st = run_query(m, d_pts, n, d_out, nullptr, &o, stream);
+    if (st) return st;
+    SAND_CUDA(cudaMemcpyAsync(h_out, d_out, (size_t)n * 4, cudaMemcpyDeviceToHost, s), "D2H values");
+    SAND_CUDA(cudaStreamSynchronize(s), "stream synchronize");
+    return SAND_OK;
+}
+
+sand_status sand_read_stats(sand_model m, const void *d_workspace, sand_query_stats *out, void *stream) {
+    g_err.clear();
+    sand_status st = model_precheck(m);
+    if (st) return st;
+    if (!out) { set_error("NULL output"); return SAND_EINVAL; }
+    const void *ws = d_workspace ? d_workspace : m->d_ws;
+    if (!ws) { set_error("no workspace"); return SAND_EINVAL; }
+    DeviceGuard g(m->device);
+    WsHeader h;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    SAND_CUDA(cudaMemcpyAsync(&h, ws, sizeof h, cudaMemcpyDeviceToHost, s), "read stats");
+    SAND_CUDA(cudaStreamSynchronize(s), "stream synchronize");
+    out->flags = h.flags;
+    out->n_network = h.n_active;
+    memcpy(out->count, h.count, sizeof out->count);
+    if (h.flags & SAND_FLAG_TIMEOUT) {
+        set_error("a device-side wait timed out (site %u)", h.timeout_where);
+        return SAND_ETIMEOUT;
+    }
+    return SAND_OK;
+}
+
+sand_status sand_model_desc(sand_model m, sand_tmlp_desc *out) {
+    g_err.clear();
+    sand_status st = model_precheck(m);
+    if (st) return st;
+    if (!out) { set_error("NULL output"); return SAND_EINVAL; }
+    *out = m->desc;
+    return SAND_OK;
+}
+
+sand_status sand_free(sand_model m) {
+    g_err.clear();
+    if (!m) return SAND_OK;
+    {
+        DeviceGuard g(m->device);
+        cudaDeviceSynchronize();
+        release(m);
+    }
+    delete m;
+    return SAND_OK;
+}
+
+}  // extern "C"

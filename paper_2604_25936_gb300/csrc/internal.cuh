@@ -1,0 +1,124 @@
+// Internal declarations of libsand (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "sand.h"
+
+namespace sand {
+
+constexpr int kMaxLayers = 14;       // exit layers 1..14; count[15] of the stats counts NaN points
+constexpr int kMaxWidth = 512;
+constexpr int kLookupThreads = 256;
+constexpr int kLookupChunk = 2048;   // points staged through shared memory per step
+constexpr int kMaxLookupBlocks = 1216;
+constexpr uint8_t kExitNaN = 0xFF;
+
+// ---------------------------------------------------------------- device views
+struct TmlpDev {
+    int L, W, D, tail_kind, act, enc, m;
+    float omega0;
+    const float *B;                 // [m][3] Fourier matrix
+    const float *WT[kMaxLayers];    // layer l (0-based): transposed weights [fan_in][W]
+    const float *bias[kMaxLayers];  // [W]
+    const float *tw;                // [L][2][W]
+    const float *tb;                // [L][2]
+};
+
+struct MapDev {
+    const uint8_t *grid;  // [R^3] exit layer per finest cell, x fastest
+    const float *far;     // [R^3] stored SDF per finest cell, or nullptr when the map has no far leaves
+    int level;            // R = 1 << level
+    int n_layers;
+};
+
+// Workspace header, at offset 0 of every query workspace.
+struct WsHeader {
+    uint32_t tile_counter;
+    uint32_t flags;
+    uint32_t n_active;          // points with exit layer >= 1
+    uint32_t n_blocks;          // lookup grid size used by the query
+    uint32_t count[16];         // points per exit layer 0..14, [15] = NaN points
+    uint32_t bin_start[16];     // first sorted row of exit layer d (rows sorted by descending d)
+    uint32_t timeout_where;
+    uint32_t pad[27];
+};
+static_assert(sizeof(WsHeader) <= 1024, "workspace header");
+
+struct WsLayout {
+    size_t header = 0, hist = 0, exit = 0, sorted = 0, total = 0;
+};
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+inline WsLayout ws_layout(int64_t n) {
+    WsLayout w;
+    w.header = 0;
+    w.hist = 1024;
+    w.exit = align_up(w.hist + sizeof(uint32_t) * 16 * kMaxLookupBlocks, 256);
+    w.sorted = align_up(w.exit + (size_t)n, 256);
+    w.total = align_up(w.sorted + (size_t)n * 16, 256);
+    return w;
+}
+
+// ---------------------------------------------------------------- device math
+// 2*pi split into three float32 parts (Cody & Waite 1980): C1 and C2 carry 16
+// significant bits each, so k*C1 and k*C2 are exact for |k| <= 128.  Derived
+// from 2*pi with 200-bit arithmetic; C1 + C2 + C3 differs from 2*pi by 4.9e-18.
+#define SAND_TWO_PI_C1 6.2830810546875f
+#define SAND_TWO_PI_C2 1.0425224900245667e-04f
+#define SAND_TWO_PI_C3 2.430840251310684e-10f
+#define SAND_INV_TWO_PI 0.15915493667125702f
+
+// sin(a) for |a| <= ~800: reduce a to r in [-pi, pi] with the split above,
+// then the hardware sine approximation on the reduced argument.
+__device__ __forceinline__ float sin_reduced(float a) {
+    float k = rintf(a * SAND_INV_TWO_PI);
+    float r = fmaf(-k, SAND_TWO_PI_C1, a);
+    r = fmaf(-k, SAND_TWO_PI_C2, r);
+    r = fmaf(-k, SAND_TWO_PI_C3, r);
+    return __sinf(r);
+}
+__device__ __forceinline__ void sincos_reduced(float a, float *s, float *c) {
+    float k = rintf(a * SAND_INV_TWO_PI);
+    float r = fmaf(-k, SAND_TWO_PI_C1, a);
+    r = fmaf(-k, SAND_TWO_PI_C2, r);
+    r = fmaf(-k, SAND_TWO_PI_C3, r);
+    __sincosf(r, s, c);
+}
+
+// Fourier features gamma_k = sin(2 pi s_k), gamma_{m+k} = cos(2 pi s_k), s_k = B_k . x.
+// s_k is accumulated as an unevaluated float32 pair (error-free products with
+// FMA and Knuth's two-sum), reduced modulo 1 exactly, so the phase error does
+// not grow with |s_k|.  Returns the reduced s in [-0.5, 0.5].
+__device__ __forceinline__ float fourier_phase(const float *Bk, float x, float y, float z) {
+    float p0 = Bk[0] * x, e0 = fmaf(Bk[0], x, -p0);
+    float p1 = Bk[1] * y, e1 = fmaf(Bk[1], y, -p1);
+    float p2 = Bk[2] * z, e2 = fmaf(Bk[2], z, -p2);
+    float s = p0 + p1;
+    float bv = s - p0;
+    float err = (p0 - (s - bv)) + (p1 - bv);
+    float s2 = s + p2;
+    bv = s2 - s;
+    err += (s - (s2 - bv)) + (p2 - bv);
+    err += e0 + e1 + e2;
+    float k = rintf(s2);
+    return (s2 - k) + err;   // s2 - k is exact (Sterbenz) for |s2| < 2^23
+}
+
+// ---------------------------------------------------------------- host helpers
+void set_error(const char *fmt, ...);
+sand_status cuda_fail(cudaError_t e, const char *what);
+
+// Kernel launchers (stream-ordered, no host synchronisation).
+cudaError_t launch_lookup(const MapDev &map, const float *pts, int64_t n, int max_depth, float *out, float *grad,
+                          uint8_t *exit_layers, void *ws, cudaStream_t s);
+cudaError_t launch_scatter(const float *pts, int64_t n, int n_layers, void *ws, cudaStream_t s);
+cudaError_t launch_tmlp_simt(const TmlpDev &M, const float *pts, int64_t n, int full_depth, void *ws,
+                             float *out, float *grad, int num_sms, cudaStream_t s);
+cudaError_t launch_init_header(void *ws, cudaStream_t s);
+
+}  // namespace sand

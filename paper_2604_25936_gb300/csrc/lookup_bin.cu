@@ -1,0 +1,214 @@
+// Depth-map lookup and exit-layer binning.
+//
+// lookup  : point -> finest cell of the depth map -> exit layer d (Sec. 3.4);
+//           d = 0 writes the stored far value (Eq. 7); LOD clamp d <- min(d, max_depth).
+// scan    : exclusive scan of the per-block exit-layer histograms in the order
+//           (d = L .. 1, block 0 .. G-1), giving every block its output offset per layer.
+// scatter : stable counting sort of the network points by descending exit layer into
+//           a packed float4 (x, y, z, original index) array read by the T-MLP kernels.
+//
+// Cell index (bit-exact with the octree descent of the oracle): for R = 2^level
+// cells per axis over [-1, 1], i = clamp(floor(x * R/2), -R/2, R/2 - 1) + R/2.
+// x * R/2 is exact in float32 (power-of-two scale), so the index equals the one
+// exact arithmetic gives, including ties at cell boundaries (upper cell) and -0.
+#include "internal.cuh"
+
+namespace sand {
+
+__device__ __forceinline__ int cell_index(float v, float hr, int half) {
+    float f = floorf(v * hr);
+    f = fminf(fmaxf(f, -hr), hr - 1.0f);
+    return (int)f + half;
+}
+
+// Stage kLookupChunk points [c0, c0 + cn) of the AoS array into shared memory.
+__device__ __forceinline__ void stage_points(float *sp, const float *pts, int64_t c0, int cn, bool vec) {
+    const int nf = cn * 3;
+    const float *src = pts + c0 * 3;
+    if (vec) {  // src is 16-byte aligned: c0 is a multiple of kLookupChunk and pts is 16-byte aligned
+        const float4 *s4 = reinterpret_cast<const float4 *>(src);
+        float4 *d4 = reinterpret_cast<float4 *>(sp);
+        const int n4 = nf >> 2;
+        for (int i = threadIdx.x; i < n4; i += blockDim.x) d4[i] = __ldg(s4 + i);
+        for (int i = (n4 << 2) + threadIdx.x; i < nf; i += blockDim.x) sp[i] = __ldg(src + i);
+    } else {
+        for (int i = threadIdx.x; i < nf; i += blockDim.x) sp[i] = __ldg(src + i);
+    }
+}
+
+__global__ void __launch_bounds__(kLookupThreads)
+lookup_kernel(MapDev map, const float *__restrict__ pts, int64_t n, int64_t per_block, int max_depth,
+              float *__restrict__ out, float *__restrict__ grad, uint8_t *__restrict__ exit_ws,
+              uint8_t *__restrict__ exit_user, WsHeader *hdr, uint32_t *__restrict__ hist, int n_blocks, int vec) {
+    __shared__ __align__(16) float sp[kLookupChunk * 3];
+    __shared__ uint32_t cnt[16];
+    if (threadIdx.x < 16) cnt[threadIdx.x] = 0;
+    const int R = 1 << map.level;
+    const int half = R >> 1;
+    const float hr = (float)R * 0.5f;
+    const int64_t start = (int64_t)blockIdx.x * per_block;
+    const int64_t end = min(n, start + per_block);
+    const int lane = threadIdx.x & 31;
+    for (int64_t c0 = start; c0 < end; c0 += kLookupChunk) {
+        const int cn = (int)min((int64_t)kLookupChunk, end - c0);
+        __syncthreads();
+        stage_points(sp, pts, c0, cn, vec != 0);
+        __syncthreads();
+        for (int k = 0; k < kLookupChunk / kLookupThreads; ++k) {
+            const int p = k * kLookupThreads + threadIdx.x;
+            int bin = 16;  // 16 = no point
+            if (p < cn) {
+                const float x = sp[3 * p], y = sp[3 * p + 1], z = sp[3 * p + 2];
+                const int64_t i = c0 + p;
+                uint8_t e;
+                if (isnan(x) || isnan(y) || isnan(z)) {
+                    e = kExitNaN;
+                    bin = 15;
+                    const float qnan = __int_as_float(0x7fc00000);
+                    if (out) out[i] = qnan;
+                    if (grad) grad[3 * i] = grad[3 * i + 1] = grad[3 * i + 2] = qnan;
+                } else {
+                    const int ix = cell_index(x, hr, half), iy = cell_index(y, hr, half), iz = cell_index(z, hr, half);
+                    const int64_t c = ((int64_t)iz * R + iy) * R + ix;
+                    int d = __ldg(map.grid + c);
+                    if (d > 0 && max_depth > 0 && d > max_depth) d = max_depth;
+                    if (d == 0) {
+                        if (out) out[i] = map.far ? __ldg(map.far + c) : 0.0f;
+                        if (grad) grad[3 * i] = grad[3 * i + 1] = grad[3 * i + 2] = 0.0f;
+                    }
+                    e = (uint8_t)d;
+                    bin = d;
+                }
+                exit_ws[i] = e;
+                if (exit_user) exit_user[i] = e;
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, bin);
+            if (bin < 16 && lane == __ffs(peers) - 1) atomicAdd(&cnt[bin], (uint32_t)__popc(peers));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 16) {
+        const uint32_t c = cnt[threadIdx.x];
+        hist[threadIdx.x * n_blocks + blockIdx.x] = c;
+        if (c) atomicAdd(&hdr->count[threadIdx.x], c);
+        if (threadIdx.x == 15 && c) atomicOr(&hdr->flags, (uint32_t)SAND_FLAG_NAN_INPUT);
+    }
+}
+
+// Single-block exclusive scan over hist[d][g] for d = L .. 1 (descending exit layer), g = 0 .. G-1.
+__global__ void __launch_bounds__(1024) scan_kernel(WsHeader *hdr, uint32_t *hist, int n_blocks, int L) {
+    __shared__ uint32_t part[1024];
+    const int total = L * n_blocks;
+    const int per = (total + blockDim.x - 1) / blockDim.x;
+    const int b0 = threadIdx.x * per, b1 = min(total, b0 + per);
+    auto at = [&](int f) -> uint32_t & { return hist[(L - f / n_blocks) * n_blocks + (f % n_blocks)]; };
+    uint32_t s = 0;
+    for (int f = b0; f < b1; ++f) s += at(f);
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {  // Hillis-Steele inclusive scan
+        uint32_t v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+    for (int f = b0; f < b1; ++f) {
+        uint32_t v = at(f);
+        if (f % n_blocks == 0) hdr->bin_start[L - f / n_blocks] = run;
+        at(f) = run;
+        run += v;
+    }
+    if (threadIdx.x == blockDim.x - 1) hdr->n_active = part[blockDim.x - 1];
+}
+
+__global__ void __launch_bounds__(kLookupThreads)
+scatter_kernel(const float *__restrict__ pts, int64_t n, int64_t per_block, const uint8_t *__restrict__ exit_ws,
+               const uint32_t *__restrict__ hist, int n_blocks, int L, float4 *__restrict__ sorted, int vec) {
+    __shared__ __align__(16) float sp[kLookupChunk * 3];
+    __shared__ uint32_t base[16], wcnt[kLookupThreads / 32][16], wpre[kLookupThreads / 32][16], tot[16];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x < 16) base[threadIdx.x] = (threadIdx.x >= 1 && threadIdx.x <= L) ? hist[threadIdx.x * n_blocks + blockIdx.x] : 0u;
+    const int64_t start = (int64_t)blockIdx.x * per_block;
+    const int64_t end = min(n, start + per_block);
+    const unsigned lt_mask = (1u << lane) - 1u;
+    for (int64_t c0 = start; c0 < end; c0 += kLookupChunk) {
+        const int cn = (int)min((int64_t)kLookupChunk, end - c0);
+        __syncthreads();
+        stage_points(sp, pts, c0, cn, vec != 0);
+        __syncthreads();
+        for (int k = 0; k < kLookupChunk / kLookupThreads; ++k) {
+            const int p = k * kLookupThreads + threadIdx.x;
+            int d = (p < cn) ? exit_ws[c0 + p] : 0;
+            const bool net = d >= 1 && d <= L;
+            const int key = net ? d : 0;
+            const unsigned peers = __match_any_sync(0xffffffffu, key);
+            const int rank = __popc(peers & lt_mask);
+            if (threadIdx.x < 16 * (kLookupThreads / 32)) (&wcnt[0][0])[threadIdx.x] = 0u;
+            __syncthreads();
+            if (net && rank == 0) wcnt[warp][d] = (uint32_t)__popc(peers);
+            __syncthreads();
+            if (threadIdx.x < 16) {
+                uint32_t acc = 0;
+                for (int w = 0; w < kLookupThreads / 32; ++w) {
+                    wpre[w][threadIdx.x] = acc;
+                    acc += wcnt[w][threadIdx.x];
+                }
+                tot[threadIdx.x] = acc;
+            }
+            __syncthreads();
+            if (net) {
+                const uint32_t pos = base[d] + wpre[warp][d] + (uint32_t)rank;
+                sorted[pos] = make_float4(sp[3 * p], sp[3 * p + 1], sp[3 * p + 2], __int_as_float((int)(c0 + p)));
+            }
+            __syncthreads();
+            if (threadIdx.x < 16) base[threadIdx.x] += tot[threadIdx.x];
+        }
+    }
+}
+
+static void lookup_grid(int64_t n, int *g, int64_t *per_block) {
+    int64_t chunks = (n + kLookupChunk - 1) / kLookupChunk;
+    int64_t blocks = chunks < kMaxLookupBlocks ? chunks : kMaxLookupBlocks;
+    if (blocks < 1) blocks = 1;
+    int64_t chunks_per_block = (chunks + blocks - 1) / blocks;
+    *per_block = chunks_per_block * kLookupChunk;
+    *g = (int)((n + *per_block - 1) / *per_block);
+    if (*g < 1) *g = 1;
+}
+
+cudaError_t launch_init_header(void *ws, cudaStream_t s) { return cudaMemsetAsync(ws, 0, sizeof(WsHeader), s); }
+
+cudaError_t launch_lookup(const MapDev &map, const float *pts, int64_t n, int max_depth, float *out, float *grad,
+                          uint8_t *exit_layers, void *ws, cudaStream_t s) {
+    WsLayout L = ws_layout(n);
+    char *base = static_cast<char *>(ws);
+    int g;
+    int64_t per;
+    lookup_grid(n, &g, &per);
+    const int vec = (reinterpret_cast<uintptr_t>(pts) & 15) == 0;
+    lookup_kernel<<<g, kLookupThreads, 0, s>>>(map, pts, n, per, max_depth, out, grad,
+                                               reinterpret_cast<uint8_t *>(base + L.exit), exit_layers,
+                                               reinterpret_cast<WsHeader *>(base), reinterpret_cast<uint32_t *>(base + L.hist),
+                                               g, vec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const float *pts, int64_t n, int n_layers, void *ws, cudaStream_t s) {
+    WsLayout L = ws_layout(n);
+    char *base = static_cast<char *>(ws);
+    int g;
+    int64_t per;
+    lookup_grid(n, &g, &per);
+    const int vec = (reinterpret_cast<uintptr_t>(pts) & 15) == 0;
+    scan_kernel<<<1, 1024, 0, s>>>(reinterpret_cast<WsHeader *>(base), reinterpret_cast<uint32_t *>(base + L.hist), g,
+                                   n_layers);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    scatter_kernel<<<g, kLookupThreads, 0, s>>>(pts, n, per, reinterpret_cast<const uint8_t *>(base + L.exit),
+                                                reinterpret_cast<const uint32_t *>(base + L.hist), g, n_layers,
+                                                reinterpret_cast<float4 *>(base + L.sorted), vec);
+    return cudaGetLastError();
+}
+
+}  // namespace sand

@@ -1,0 +1,20 @@
+// Tensor-core (tcgen05) T-MLP path: packed weights and launcher.
+#pragma once
+
+#include "internal.cuh"
+
+namespace sand {
+
+struct TcModel {
+    int packed_precision = -1;   // precision the packed buffers hold, -1 = none
+    void *d_pack = nullptr;      // packed weights / biases / tails
+    size_t pack_bytes = 0;
+};
+
+bool tc_supported(const sand_tmlp_desc &d, int precision);
+sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params, int precision);
+cudaError_t launch_tmlp_tc(const TcModel &tc, const sand_tmlp_desc &d, int precision, const float *pts, int64_t n,
+                           int full_depth, void *ws, float *out, int num_sms, cudaStream_t s);
+void tc_release(TcModel *tc);
+
+}  // namespace sand

@@ -1,0 +1,283 @@
+"""Parity of the CUDA query path (through the C-ABI) with the FP64 oracle.
+
+Exit layers must match bit-exactly; SDF values within the stated tolerance:
+1e-5 absolute for the float32 paths, 2e-3 for the 16-bit tensor-core paths.
+Gradients: omega0 x the value tolerance (each derivative of sin(omega0 u)
+brings one factor omega0 into the sensitivity to rounding).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+# precisions the library implements, with their value tolerance
+TOL = {"fp32_simt": 1e-5, "fp32": 1e-5, "fp16": 2e-3, "bf16": 2e-3}
+IMPLEMENTED = ["fp32_simt"]
+
+
+def _lib():
+    from paper_2604_25936_gb300 import Model, SandError
+    return Model, SandError
+
+
+def load(model, tree=None, device=0):
+    Model, _ = _lib()
+    m = Model.from_params(*model.header_ints(), model.omega0, model.flat(), device=device)
+    if tree is not None:
+        m.set_depth_map(tree.max_level, tree.n_layers, tree.child, tree.depth, tree.far)
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    model, tree, pts = synth.config_tiny()
+    return model, tree, pts, load(model, tree)
+
+
+@pytest.fixture(scope="module")
+def scene():
+    model = synth.siren_tmlp(8, 256, seed=1)
+    tree = synth.scene_octree(7, 8)
+    return model, tree, load(model, tree)
+
+
+def check(y_gpu, y_ref, tol, what=""):
+    y = y_gpu.double().cpu().numpy() if isinstance(y_gpu, torch.Tensor) else y_gpu
+    both_nan = np.isnan(y) & np.isnan(y_ref)
+    assert np.array_equal(np.isnan(y), np.isnan(y_ref)), what + ": NaN pattern differs"
+    err = np.abs(np.where(both_nan, 0, y - y_ref))
+    worst = int(np.argmax(err)) if err.size else 0
+    assert err.size == 0 or err.max() <= tol, "%s: max |err| %.3g at %d (tol %g)" % (what, err.max(), worst, tol)
+    return float(err.max()) if err.size else 0.0
+
+
+@pytest.mark.parametrize("prec", IMPLEMENTED)
+def test_tiny_parity(tiny, prec):
+    model, tree, pts, m = tiny
+    y_ref, d_ref = oracle.query(model, tree, pts, exit_layers=True)
+    y, el = m.query(dev(pts), precision=prec, exit_layers=True)
+    np.testing.assert_array_equal(el.cpu().numpy().astype(np.int32), d_ref)
+    check(y, y_ref, TOL[prec], "tiny/" + prec)
+    st = m.stats()
+    assert st["count"][1:5] == [19456, 8192, 3584, 1536] and st["n_network"] == 32768 and st["flags"] == 0
+
+
+@pytest.mark.parametrize("prec", IMPLEMENTED)
+def test_scene_lattice_parity(scene, prec):
+    """8 x 256 SIREN on its level-7 octree, 64^3 lattice: every tile size and a ragged tail per layer."""
+    model, tree, m = scene
+    pts = synth.lattice(64)
+    y_ref, d_ref = oracle.query(model, tree, pts, exit_layers=True)
+    y, el = m.query(dev(pts), precision=prec, exit_layers=True)
+    np.testing.assert_array_equal(el.cpu().numpy().astype(np.int32), d_ref)
+    check(y, y_ref, TOL[prec], "scene64/" + prec)
+    st = m.stats()
+    assert st["count"][:9] == np.bincount(d_ref, minlength=9).tolist()
+
+
+@pytest.mark.parametrize("prec", IMPLEMENTED)
+def test_full_depth_parity(scene, prec):
+    """full_depth = the plain T-MLP to layer L at every point (the baseline of the benchmark)."""
+    model, tree, m = scene
+    pts = synth.uniform_points(20001, seed=17)
+    y_ref = oracle.full_depth(model, pts)
+    y = m.query(dev(pts), precision=prec, full_depth=True)
+    check(y, y_ref, TOL[prec], "full/" + prec)
+
+
+@pytest.mark.parametrize("prec", IMPLEMENTED)
+def test_mult_tails_far_field_lod(prec):
+    """Multiplicative tails (Eq. 3), far leaves answered from the map (Eq. 7), LOD clamps."""
+    model = synth.siren_tmlp(8, 256, seed=1, tail_kind=synth.TAIL_MULT)
+    tree = synth.scene_octree(7, 8, far_field=True)
+    m = load(model, tree)
+    pts = synth.lattice(48)
+    for lod in (0, 2, 5):
+        y_ref, d_ref = oracle.query(model, tree, pts, max_depth=lod, exit_layers=True)
+        assert (d_ref == 0).any()
+        y, el = m.query(dev(pts), precision=prec, max_depth=lod, exit_layers=True)
+        np.testing.assert_array_equal(el.cpu().numpy().astype(np.int32), d_ref)
+        z = d_ref == 0
+        np.testing.assert_array_equal(y.cpu().numpy()[z], y_ref[z].astype(np.float32))
+        check(y, y_ref, TOL[prec], "mult/far/lod%d/%s" % (lod, prec))
+    m.free()
+
+
+@pytest.mark.parametrize("prec", IMPLEMENTED)
+def test_edge_cases(tiny, scene, prec):
+    """Empty, single, ragged and misaligned inputs; NaN, outside-domain and cell-boundary points."""
+    Model, SandError = _lib()
+    model, tree, m = scene
+    out = m.query(torch.empty((0, 3), device="cuda"), precision=prec)
+    assert out.numel() == 0
+    g = np.random.Generator(np.random.PCG64(3))
+    for n in (1, 2, 127, 128, 129, 255, 257, 1000, 4097):
+        pts = g.uniform(-1, 1, (n, 3)).astype(np.float32)
+        check(m.query(dev(pts), precision=prec), oracle.query(model, tree, pts), TOL[prec], "n=%d" % n)
+    # points not 16-byte aligned: a view starting one float into the buffer
+    base = dev(g.uniform(-1, 1, 3 * 5001 + 1).astype(np.float32))
+    view = base[1:].view(5001, 3)
+    assert view.data_ptr() % 16 != 0
+    check(m.query(view, precision=prec), oracle.query(model, tree, view.cpu().numpy()), TOL[prec], "misaligned")
+    # boundaries, outside, NaN: exit layers bit-exact, NaN propagated and flagged
+    pts = np.concatenate([synth.boundary_points(7), g.uniform(-3, 3, (500, 3)).astype(np.float32)])
+    pts[5] = [np.nan, 0, 0]
+    pts[600] = [0, 0, np.nan]
+    y_ref, d_ref = oracle.query(model, tree, pts, exit_layers=True)
+    y, el = m.query(dev(pts), precision=prec, exit_layers=True)
+    e = el.cpu().numpy().astype(np.int32)
+    e[e == 255] = -1
+    np.testing.assert_array_equal(e, d_ref)
+    check(y, y_ref, TOL[prec], "edges")
+    assert m.stats()["flags"] & 1
+
+
+@pytest.mark.parametrize("prec", IMPLEMENTED)
+def test_relu_fourier_model(prec):
+    """6 x 128 ReLU T-MLP on 64 Fourier features (sigma 10) with its own octree."""
+    model = synth.relu_ff_tmlp(6, 128, n_freq=64, sigma=10.0, seed=3)
+    tree = synth.scene_octree(7, 6, transform=synth.rotation([1, 1, 0], 0.7), scale=0.9)
+    m = load(model, tree)
+    pts = synth.lattice(40)
+    y_ref, d_ref = oracle.query(model, tree, pts, exit_layers=True)
+    y, el = m.query(dev(pts), precision=prec, exit_layers=True)
+    np.testing.assert_array_equal(el.cpu().numpy().astype(np.int32), d_ref)
+    scale = max(1.0, float(np.abs(y_ref).max()))
+    check(y, y_ref, TOL[prec] * scale, "relu-ff/" + prec)
+    m.free()
+
+
+def test_closed_form_sphere_on_gpu():
+    """Hand-built ReLU model: y_4 = |x|^2 - r^2 exactly in real arithmetic; gradient 2x."""
+    model = synth.relu_sphere_tmlp(0.6, width=64)
+    m = load(model)
+    pts = synth.uniform_points(3000, seed=5)
+    p = pts.astype(np.float64)
+    y, gr = m.query_grad(dev(pts), precision="fp32_simt", full_depth=True)
+    check(y, (p ** 2).sum(1) + float(np.float32(-0.36)), 1e-6, "sphere")
+    check(gr.double().cpu().numpy().ravel(), (2 * p).ravel(), 1e-6, "sphere grad")
+    m.free()
+
+
+@pytest.mark.parametrize("kind", ["siren", "siren_mult", "relu_ff"])
+def test_gradient_parity(kind):
+    """dy/dx against the oracle gradient and against central differences of the oracle (h = 1e-4)."""
+    if kind == "siren":
+        model, tree = synth.siren_tmlp(8, 256, seed=1), synth.scene_octree(7, 8)
+    elif kind == "siren_mult":
+        model, tree = synth.siren_tmlp(8, 256, seed=1, tail_kind=synth.TAIL_MULT), synth.scene_octree(7, 8, far_field=True)
+    else:
+        model, tree = synth.relu_ff_tmlp(6, 128, n_freq=64, sigma=10.0, seed=3), synth.scene_octree(7, 6)
+    m = load(model, tree)
+    pts = synth.uniform_points(6000, seed=23)
+    y_ref, g_ref, d_ref = oracle.query(model, tree, pts, grad=True, exit_layers=True)
+    y, g = m.query_grad(dev(pts), precision="fp32_simt")
+    vscale = max(1.0, float(np.abs(y_ref).max()))
+    check(y, y_ref, 1e-5 * vscale, kind + " value")
+    gscale = max(1.0, float(np.abs(g_ref).max()))
+    w0 = model.omega0 if model.activation == synth.ACT_SINE else 30.0
+    g_gpu = g.double().cpu().numpy()
+    check(g_gpu.ravel(), g_ref.ravel(), 1e-5 * w0 * gscale, kind + " grad")
+    # central differences of the oracle at float32-representable steps
+    net = np.where(d_ref > 0)[0][:400]
+    fd = np.zeros((len(net), 3))
+    for a in range(3):
+        pp, pm = pts[net].copy(), pts[net].copy()
+        pp[:, a] += np.float32(1e-4)
+        pm[:, a] -= np.float32(1e-4)
+        step = pp[:, a].astype(np.float64) - pm[:, a].astype(np.float64)
+        fd[:, a] = (oracle.evaluate(model, pp, d_ref[net]) - oracle.evaluate(model, pm, d_ref[net])) / step
+    trunc = 1e-4 ** 2 * w0 ** 3 * gscale  # |f'''| h^2 bound for a sine network
+    check(g_gpu[net].ravel(), fd.ravel(), 1e-5 * w0 * gscale + trunc, kind + " grad vs FD")
+    m.free()
+
+
+def test_autograd_function(scene):
+    from paper_2604_25936_gb300 import SandSDF
+    model, tree, m = scene
+    pts = synth.uniform_points(777, seed=29)
+    x = dev(pts).requires_grad_(True)
+    y = SandSDF.apply(x, m, "fp32_simt")
+    w = torch.linspace(-1, 1, 777, device="cuda")
+    (y * w).sum().backward()
+    _, g_ref = oracle.query(model, tree, pts, grad=True)
+    check(x.grad.double().cpu().numpy().ravel(), (g_ref * np.linspace(-1, 1, 777)[:, None]).ravel(),
+          3e-4 * max(1.0, float(np.abs(g_ref).max())), "autograd")
+
+
+def test_file_loaders_match_memory(tmp_path, scene):
+    Model, _ = _lib()
+    model, tree, m = scene
+    mp, tp = str(tmp_path / "m.tmlp"), str(tmp_path / "t.sdmo")
+    synth.save_tmlp(mp, model)
+    synth.save_octree(tp, tree)
+    mf = Model.from_file(mp, device=0)
+    mf.load_depth_map(tp)
+    pts = dev(synth.uniform_points(10000, seed=31))
+    a = m.query(pts, precision="fp32_simt")
+    b = mf.query(pts, precision="fp32_simt")
+    assert torch.equal(a, b)
+    mf.free()
+
+
+def test_errors(scene):
+    Model, SandError = _lib()
+    model, tree, _ = scene
+    m = load(model)
+    with pytest.raises(SandError, match="ENOMAP"):
+        m.query(dev(synth.uniform_points(10, 1)), precision="fp32_simt")
+    m.set_depth_map(tree.max_level, tree.n_layers, tree.child, tree.depth, tree.far)
+    small = torch.empty(64, dtype=torch.uint8, device="cuda")
+    with pytest.raises(SandError, match="EINVAL"):
+        m.query(dev(synth.uniform_points(10, 1)), precision="fp32_simt", workspace=small)
+    bad = tree.depth.copy()
+    bad[np.where(tree.child < 0)[0][0]] = 9
+    with pytest.raises(SandError, match="EFORMAT"):
+        m.set_depth_map(tree.max_level, tree.n_layers, tree.child, bad, tree.far)
+    m.free()
+
+
+def test_host_query_and_streams(scene):
+    model, tree, m = scene
+    pts = synth.uniform_points(50000, seed=37)
+    ref = m.query(dev(pts), precision="fp32_simt").cpu()
+    hp = torch.from_numpy(pts).pin_memory()
+    ho = torch.empty(50000, dtype=torch.float32).pin_memory()
+    m.query_host(hp, out=ho, precision="fp32_simt")
+    assert torch.equal(ho, ref)
+    s = torch.cuda.Stream()
+    x = dev(pts)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        ws = torch.empty(m.workspace_bytes(50000) + 256, dtype=torch.uint8, device="cuda")
+        y = m.query(x, precision="fp32_simt", workspace=ws, stream=s)
+    s.synchronize()
+    assert torch.equal(y.cpu(), ref)
+
+
+@pytest.mark.parametrize("prec", IMPLEMENTED)
+def test_full_size_lattice_sampled(scene, prec):
+    """256^3 lattice (16.7M points) in the launch configuration the benchmark times:
+    exit layers bit-exact at every point; SDF checked on 20,000 sampled points."""
+    model, tree, m = scene
+    n = 256
+    pts = synth.lattice(n)
+    x = dev(pts)
+    ws = m.workspace(len(pts))
+    y, el = m.query(x, precision=prec, exit_layers=True, workspace=ws)
+    d_ref, _ = oracle.lookup(tree, pts)
+    np.testing.assert_array_equal(el.cpu().numpy().astype(np.int32), d_ref)
+    idx = synth.sample_indices(len(pts), 20000, seed=11)
+    y_ref = oracle.query(model, tree, pts[idx])
+    check(y.cpu().numpy()[idx].astype(np.float64), y_ref, TOL[prec], "256^3 sampled/" + prec)
