@@ -185,7 +185,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sand", choices=["sand", "reference"])
-    ap.add_argument("--precision", default="fp32_simt", choices=sorted(TOL))
+    ap.add_argument("--precision", default="fp32", choices=sorted(TOL))
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     args = ap.parse_args()
     if args.impl == "reference":

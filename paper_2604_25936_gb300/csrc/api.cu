@@ -381,7 +381,7 @@ static sand_status run_query(sand_model m, const float *d_points, int64_t n, flo
     } else {
         st = tc_prepare(&m->tc, m->desc, m->params.data(), o.precision);
         if (st) return st;
-        SAND_CUDA(launch_tmlp_tc(m->tc, m->desc, o.precision, d_points, n, o.full_depth, ws, d_out, m->num_sms, s),
+        SAND_CUDA(launch_tmlp_tc(m->tc, m->simt, d_points, n, o.full_depth, ws, d_out, m->num_sms, s),
                   "tensor-core T-MLP kernel");
     }
     if (ev) SAND_CUDA(cudaEventRecord(ev[2], s), "event record");

@@ -7,14 +7,15 @@ namespace sand {
 
 struct TcModel {
     int packed_precision = -1;   // precision the packed buffers hold, -1 = none
-    void *d_pack = nullptr;      // packed weights / biases / tails
+    void *d_pack = nullptr;      // packed hidden-layer weights (fp16 / bf16, K-major rows)
     size_t pack_bytes = 0;
+    void *host = nullptr;        // tensor map and kernel parameters
 };
 
 bool tc_supported(const sand_tmlp_desc &d, int precision);
 sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params, int precision);
-cudaError_t launch_tmlp_tc(const TcModel &tc, const sand_tmlp_desc &d, int precision, const float *pts, int64_t n,
-                           int full_depth, void *ws, float *out, int num_sms, cudaStream_t s);
+cudaError_t launch_tmlp_tc(const TcModel &tc, const TmlpDev &M, const float *pts, int64_t n, int full_depth, void *ws,
+                           float *out, int num_sms, cudaStream_t s);
 void tc_release(TcModel *tc);
 
 }  // namespace sand
