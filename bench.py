@@ -179,6 +179,29 @@ def run_reference(args):
     return 0
 
 
+def run_profile_case(args):
+    """The same model and map as the benchmark on a smaller point set, for ncu captures."""
+    import torch
+    import paper_2604_25936_gb300 as sand
+    from paper_2604_25936_gb300 import build as sand_build
+    sand_build.build()
+    model = synth.siren_tmlp(N_LAYERS, WIDTH, seed=SEED)
+    tree = synth.scene_octree(7, N_LAYERS)
+    m = sand.Model.from_params(*model.header_ints(), model.omega0, model.flat(), device=0)
+    m.set_depth_map(tree.max_level, tree.n_layers, tree.child, tree.depth, tree.far)
+    full = args.profile == "full"
+    pts = synth.uniform_points(args.grid ** 3, seed=1) if full else synth.lattice(args.grid)
+    x = torch.from_numpy(pts).cuda()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for _ in range(args.warmup + args.steps):
+        y = m.query(x, precision=args.precision, full_depth=full, events=ev)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.profile, "points": len(pts), "precision": args.precision,
+                      "tmlp_ms": ev[1].elapsed_time(ev[2]), "max_abs_y": float(y.abs().max())}), flush=True)
+    m.free()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -187,9 +210,15 @@ def main():
     ap.add_argument("--impl", default="sand", choices=["sand", "reference"])
     ap.add_argument("--precision", default="fp32", choices=sorted(TOL))
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--profile", choices=["sand", "full"], default=None,
+                    help="small profiling case: only (warmup + steps) SAND queries on a grid^3 lattice, or full-depth "
+                         "queries on grid^3 uniform points; prints one line")
+    ap.add_argument("--grid", type=int, default=GRID)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile:
+        return run_profile_case(args)
 
     import torch
     import torch.distributed as dist
