@@ -162,6 +162,24 @@ sand_status sand_query_sdf_grad(sand_model m, const float *d_points, int64_t n, 
 sand_status sand_query_sdf_host(sand_model m, const float *h_points, int64_t n, float *h_out,
                                 const sand_query_opts *opts, void *stream);
 
+/* No counterpart in the paper.  sand_query_sdf for callers that must not
+ * allocate device memory during a query: for example a host framework whose
+ * own memory pool owns the GPU's budget, or a latency-critical serving loop
+ * that cannot afford cudaMalloc's implicit device synchronisation.  Same
+ * arguments and results as sand_query_sdf, but opts->d_workspace must be NULL:
+ * the scratch comes from one static device array inside libsand sized for
+ * SAND_NOALLOC_MAX_POINTS points (about 17 MiB), which each GPU using it keeps
+ * until the process exits.  n above SAND_NOALLOC_MAX_POINTS returns
+ * SAND_EINVAL.  Nothing is allocated: the precision's device weights must
+ * already exist (SAND_FP32_SIMT always; a tensor-core precision after one
+ * sand_query_sdf with it), else SAND_EUNSUPPORTED.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress), so make it
+ * before any stream capture.  Calls share the array: calls that may overlap on
+ * the GPU (unordered streams) race and corrupt each other's results. */
+#define SAND_NOALLOC_MAX_POINTS (1 << 20)
+sand_status sand_query_sdf_noalloc(sand_model m, const float *d_points, int64_t n, float *d_out,
+                                   const sand_query_opts *opts, void *stream);
+
 /* Flags and counters a query leaves in its workspace (read after the query's
  * stream has been synchronised by this call). */
 #define SAND_FLAG_NAN_INPUT 1u

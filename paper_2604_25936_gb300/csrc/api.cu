@@ -207,6 +207,13 @@ static sand_status model_precheck(sand_model m) {
     return SAND_OK;
 }
 
+int model_device(sand_model m) { return m->device; }
+bool model_has_map(sand_model m) { return m->map_level >= 0; }
+bool model_precision_ready(sand_model m, int precision) {
+    if (precision == SAND_FP32_SIMT) return true;
+    return m->tc.packed_precision == precision && m->tc.d_pack != nullptr;
+}
+
 }  // namespace sand
 
 using namespace sand;

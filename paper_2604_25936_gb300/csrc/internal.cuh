@@ -52,9 +52,9 @@ struct WsLayout {
     size_t header = 0, hist = 0, exit = 0, sorted = 0, total = 0;
 };
 
-inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-inline WsLayout ws_layout(int64_t n) {
+constexpr WsLayout ws_layout(int64_t n) {
     WsLayout w;
     w.header = 0;
     w.hist = 1024;
@@ -120,5 +120,10 @@ cudaError_t launch_scatter(const float *pts, int64_t n, int n_layers, void *ws, 
 cudaError_t launch_tmlp_simt(const TmlpDev &M, const float *pts, int64_t n, int full_depth, void *ws,
                              float *out, float *grad, int num_sms, cudaStream_t s);
 cudaError_t launch_init_header(void *ws, cudaStream_t s);
+
+// Model facts for entry points outside api.cu.
+int model_device(sand_model m);
+bool model_has_map(sand_model m);
+bool model_precision_ready(sand_model m, int precision);  // device weights for `precision` exist already
 
 }  // namespace sand
