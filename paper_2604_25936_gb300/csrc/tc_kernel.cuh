@@ -8,15 +8,19 @@
 //   warp 1      owns the TMEM accumulator (W fp32 columns) and issues tcgen05.mma
 //               from one thread.  Each layer is two accumulators, D0 = units
 //               [0, W/2) and D1 = [W/2, W), computed one after the other.
-//   warps 2..5  epilogue of D0, warps 6..9 epilogue of D1.  Thread (quadrant q,
-//               lane i) owns tile row 32 q + i (TMEM lane restriction).  Layer 1
-//               (on the CUDA cores, float32), bias, sine, tails, the running sum
-//               y_l = y_{l-1} + t_l and the write at each row's exit layer; the new
-//               activations go back to shared memory as the next A operand.
-// Overlap: while D1's MMAs run, warps 2-5 turn D0 into activations.  D1 reads the
-// first K-half of A first and commits a barrier (a0_free) once it has, so warps
-// 2-5 may overwrite that half with the next layer's input; the next layer's MMAs
-// on that K-half start while warps 6-9 are still finishing D1.
+//   warps 2..9  epilogue.  Thread (quadrant q, lane i) owns tile row 32 q + i (the
+//               TMEM lane restriction); warps 2-5 take the first quarter of the
+//               units of each N-half, warps 6-9 the second.  Layer 1 (float32, on
+//               the CUDA cores), bias, sine, tails, the running sum
+//               y_l = y_{l-1} + t_l and the write at each row's exit layer.  The new
+//               activations are packed to fp16 and written with tcgen05.st into
+//               TMEM, where the next layer's MMAs read them as the A operand.
+// TMEM columns: [0, W) accumulator (D0 | D1), then A_hi (W/2 columns of packed
+// fp16 pairs) and, in the float32 mode, A_lo.
+// Overlap: all epilogue warps turn D0 into activations while D1's MMAs run.  D1
+// reads the first K-half of A first and commits a barrier (a0_free) once it has,
+// so D0's results may replace that half; the next layer's MMAs on that K-half
+// start while D1's results are still being written.
 // A tile runs to the exit layer of its first (deepest) row; rows whose exit layer
 // was reached ride along only in the one tile per exit layer that straddles two
 // layers; tiles of exit layer 1 never touch the tensor cores.
@@ -46,9 +50,9 @@ constexpr int kTileM = 128;
 constexpr int kEpiThreads = 256;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 constexpr int kSmemBudget = 227 * 1024;
-constexpr int kMaxStages = 8;
+constexpr int kMaxStages = 12;
 constexpr int kNumBars = 2 * kMaxStages + 8;  // full, empty, a_ready[2], d_full[2], a0_free, drain, x_full, x_empty
-// bytes after the operand tiles and constants: barriers, TMEM slot + abort flag, tail exchange
+// bytes after the weight stages and constants: barriers, TMEM slot + abort flag, tail exchange
 constexpr int kMiscBytes = kNumBars * 8 + 16 + 1024;
 
 struct TcParams {
@@ -57,8 +61,7 @@ struct TcParams {
     int kpad;                 // padded K of the packed weight matrix (multiple of 64)
     int n_stages;
     uint32_t stage_bytes;     // (W / 2) * 128
-    uint32_t a_part_bytes;    // 128 * kpad * 2
-    uint32_t tmem_cols;
+    uint32_t tmem_cols;       // power of two >= W + parts * W / 2
     float c1[kMaxLayers];     // per layer: w0 / (2 pi s) (sine) or 1 / s (ReLU)
     const float *cvec;        // [L][3][W]: bias' (w0 b / 2 pi for sine, b for ReLU), tail a, tail b
     const float *w1p;         // [3][W] first-layer weights (times w0 / 2 pi for sine), transposed
@@ -137,11 +140,22 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b,
         "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
+// D[128 x N] (+)= A[128 x 16] . B[N x 16]^T with A read from TMEM (lane = row, 32-bit
+// column = two consecutive fp16/bf16 K-elements).
+__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
-    uint32_t r[32];
+// TMEM -> registers, 32 or 16 consecutive columns of this thread's lane (asynchronous:
+// the values may be used only after tmem_wait_ld()).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t *r) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
         "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
@@ -151,10 +165,31 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// registers -> TMEM, 16 or 8 consecutive 32-bit columns of this thread's lane.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t *v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr), "r"(v[0]),
+                 "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // ------------------------------------------------------------------ helpers
 __device__ __forceinline__ int tc_row_depth(const WsHeader *hdr, uint32_t r, int L) {
@@ -176,43 +211,96 @@ __device__ __forceinline__ float activate(float t) {
     return sin_rev(t);
 }
 
+// Two activations -> one packed 16-bit pair (low half = first element) and, in the
+// float32 mode, the pair of residuals h - fp16(h).
 template <int MODE>
-__device__ __forceinline__ void pack8(const float *h, uint4 &hi, uint4 &lo) {
-    uint32_t H[4], Lo[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        if (MODE == TC_BF16) {
-            __nv_bfloat162 b = __floats2bfloat162_rn(h[2 * i], h[2 * i + 1]);
-            H[i] = *reinterpret_cast<uint32_t *>(&b);
-            Lo[i] = 0;
+__device__ __forceinline__ void pack2(float a, float b, uint32_t &hi, uint32_t &lo) {
+    if (MODE == TC_BF16) {
+        __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+        hi = *reinterpret_cast<uint32_t *>(&v);
+        lo = 0;
+    } else {
+        __half2 v = __floats2half2_rn(a, b);
+        hi = *reinterpret_cast<uint32_t *>(&v);
+        if (MODE == TC_SPLIT16) {
+            const float2 back = __half22float2(v);
+            __half2 l = __floats2half2_rn(a - back.x, b - back.y);
+            lo = *reinterpret_cast<uint32_t *>(&l);
         } else {
-            __half2 a = __floats2half2_rn(h[2 * i], h[2 * i + 1]);
-            H[i] = *reinterpret_cast<uint32_t *>(&a);
-            if (MODE == TC_SPLIT16) {
-                const float2 back = __half22float2(a);
-                __half2 l = __floats2half2_rn(h[2 * i] - back.x, h[2 * i + 1] - back.y);
-                Lo[i] = *reinterpret_cast<uint32_t *>(&l);
-            } else {
-                Lo[i] = 0;
-            }
+            lo = 0;
         }
     }
-    hi = make_uint4(H[0], H[1], H[2], H[3]);
-    lo = make_uint4(Lo[0], Lo[1], Lo[2], Lo[3]);
 }
 
-// Store 8 consecutive activations (columns j .. j+7, j % 8 == 0) of row r into the swizzled A operand.
-template <int MODE>
-__device__ __forceinline__ void store_a8(uint8_t *a_base, uint32_t a_part_bytes, int r, int j, const float *h) {
-    uint4 hi, lo;
-    pack8<MODE>(h, hi, lo);
-    const int kb = j >> 6, c = (j & 63) >> 3;
-    const uint32_t off = (uint32_t)kb * 16384u + (uint32_t)r * 128u + (uint32_t)((c ^ (r & 7)) << 4);
-    *reinterpret_cast<uint4 *>(a_base + off) = hi;
-    if (MODE == TC_SPLIT16) *reinterpret_cast<uint4 *>(a_base + a_part_bytes + off) = lo;
+template <int CH>
+__device__ __forceinline__ void tmem_ld_ch(uint32_t taddr, uint32_t *r) {
+    if (CH == 32) tmem_ld32(taddr, r);
+    else tmem_ld16(taddr, r);
+}
+template <int CH>
+__device__ __forceinline__ void tmem_st_half(uint32_t taddr, const uint32_t *v) {  // CH / 2 packed columns
+    if (CH == 32) tmem_st16(taddr, v);
+    else tmem_st8(taddr, v);
 }
 
 // ------------------------------------------------------------------ the kernel
+// One N-half of a tensor-core layer for this thread's row: NCH chunks of CH accumulator
+// columns starting at unit u0 -> bias, activation, tail partial sums and (write_a) the
+// packed activations into TMEM as the next A operand.  Both chunks are loaded before one wait.
+template <int MODE, int ACT, int TAIL, int CH, int NCH>
+__device__ __forceinline__ void epilogue_half(const TcParams &P, const float *cs, float c1, uint32_t t_lane, int u0,
+                                              bool write_a, uint32_t a_hi, uint32_t a_lo, volatile int *abort,
+                                              WsHeader *hdr, uint64_t *a0_free, uint32_t &pf, bool &pending_free,
+                                              bool first_half, float &sa, float &sb, bool &ok) {
+    constexpr bool MULT = TAIL == SAND_TAIL_MULT;
+    const int W = P.W;
+    uint32_t v[NCH][CH];
+#pragma unroll
+    for (int ci = 0; ci < NCH; ++ci) tmem_ld_ch<CH>(t_lane + (uint32_t)(u0 + ci * CH), v[ci]);
+    tmem_wait_ld();
+#pragma unroll
+    for (int ci = 0; ci < NCH; ++ci) {
+        const int c0 = u0 + ci * CH;
+        uint32_t phi[CH / 2], plo[CH / 2];
+#pragma unroll
+        for (int g = 0; g < CH / 8; ++g) {
+            const int j0 = c0 + 8 * g;
+            const float4 ba = *reinterpret_cast<const float4 *>(cs + j0);
+            const float4 bb = *reinterpret_cast<const float4 *>(cs + j0 + 4);
+            const float4 aa = *reinterpret_cast<const float4 *>(cs + W + j0);
+            const float4 ab4 = *reinterpret_cast<const float4 *>(cs + W + j0 + 4);
+            const float bv[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
+            const float av[8] = {aa.x, aa.y, aa.z, aa.w, ab4.x, ab4.y, ab4.z, ab4.w};
+            float tbv[8];
+            if (MULT) {
+                const float4 t0 = *reinterpret_cast<const float4 *>(cs + 2 * W + j0);
+                const float4 t1 = *reinterpret_cast<const float4 *>(cs + 2 * W + j0 + 4);
+                tbv[0] = t0.x; tbv[1] = t0.y; tbv[2] = t0.z; tbv[3] = t0.w;
+                tbv[4] = t1.x; tbv[5] = t1.y; tbv[6] = t1.z; tbv[7] = t1.w;
+            }
+            float h8[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float hv = activate<ACT>(fmaf(__uint_as_float(v[ci][8 * g + i]), c1, bv[i]));
+                h8[i] = hv;
+                sa = fmaf(av[i], hv, sa);
+                if (MULT) sb = fmaf(tbv[i], hv, sb);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) pack2<MODE>(h8[2 * i], h8[2 * i + 1], phi[4 * g + i], plo[4 * g + i]);
+        }
+        if (write_a) {
+            if (first_half && pending_free) {  // D1's MMAs have read the first K-half of A
+                ok = mbar_wait(smem_u32(a0_free), pf, abort, hdr, 5, false) && ok;
+                pf ^= 1;
+                pending_free = false;
+            }
+            tmem_st_half<CH>(a_hi + (uint32_t)(c0 >> 1), phi);
+            if (MODE == TC_SPLIT16) tmem_st_half<CH>(a_lo + (uint32_t)(c0 >> 1), plo);
+        }
+    }
+}
+
 template <int MODE, int ACT, int TAIL>
 __global__ void __launch_bounds__(kTcThreads, 1)
 tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const float *__restrict__ pts,
@@ -223,22 +311,22 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int W = P.W, L = P.L;
     const int hw = W >> 1;
-    uint8_t *a_base = smem;
-    uint8_t *stage_base = smem + PARTS * P.a_part_bytes;
-    float *c_l1 = reinterpret_cast<float *>(stage_base + (size_t)P.n_stages * P.stage_bytes);  // [5][W]: w1p x3, bias', a
-    float *c_ring = c_l1 + 5 * W;                                                              // [2][3][W]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(c_ring + 6 * W);
+    const int quarter = W >> 2;
+    uint8_t *stage_base = smem;
+    float *c_l1 = reinterpret_cast<float *>(stage_base + (size_t)P.n_stages * P.stage_bytes);  // [3][W] first-layer weights
+    float *c_all = c_l1 + 3 * W;                                                                // [L][3][W]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(c_all + (size_t)3 * L * W);
     uint64_t *full_bar = bars;
     uint64_t *empty_bar = bars + kMaxStages;
     uint64_t *a_ready = bars + 2 * kMaxStages;  // [2]
     uint64_t *d_full = a_ready + 2;             // [2]
     uint64_t *a0_free = d_full + 2;
     uint64_t *drain = a0_free + 1;
-    uint64_t *x_full = drain + 1;   // tail partials of the D1 warps written (128 arrivals)
-    uint64_t *x_empty = x_full + 1; // ... and read by the D0 warps (128 arrivals)
+    uint64_t *x_full = drain + 1;   // tail partials of warps 6-9 written (128 arrivals)
+    uint64_t *x_empty = x_full + 1; // ... and read by warps 2-5 (128 arrivals)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + kNumBars);
     volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
-    float *tailx = reinterpret_cast<float *>(tmem_slot + 4);  // [2 values][128 rows] from the D1 warps
+    float *tailx = reinterpret_cast<float *>(tmem_slot + 4);  // [2 values][128 rows]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n_rows = full_depth ? n : (int64_t)hdr->n_active;
@@ -250,8 +338,8 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             mbar_init(smem_u32(&full_bar[s]), 1);
             mbar_init(smem_u32(&empty_bar[s]), 1);
         }
-        mbar_init(smem_u32(&a_ready[0]), 4);
-        mbar_init(smem_u32(&a_ready[1]), 4);
+        mbar_init(smem_u32(&a_ready[0]), 8);
+        mbar_init(smem_u32(&a_ready[1]), 8);
         mbar_init(smem_u32(&d_full[0]), 1);
         mbar_init(smem_u32(&d_full[1]), 1);
         mbar_init(smem_u32(a0_free), 1);
@@ -267,16 +355,16 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (warp >= 2 && P.first_mma == 2) {  // first-layer constants: w1p (3 rows), bias', tail a
-        for (int i = threadIdx.x - 64; i < 5 * W; i += kEpiThreads) {
-            const int row = i / W, j = i % W;
-            c_l1[i] = row < 3 ? P.w1p[row * W + j] : P.cvec[(row - 3) * W + j];
-        }
+    if (warp >= 2) {  // constants of every layer, resident for the whole kernel
+        for (int i = threadIdx.x - 64; i < 3 * L * W; i += kEpiThreads) c_all[i] = __ldg(P.cvec + i);
+        if (P.first_mma == 2)
+            for (int i = threadIdx.x - 64; i < 3 * W; i += kEpiThreads) c_l1[i] = __ldg(P.w1p + i);
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    const uint32_t a_hi = tmem + (uint32_t)W, a_lo = tmem + (uint32_t)(W + hw);
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
@@ -315,7 +403,6 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             const uint32_t ab = MODE == TC_BF16 ? 1u : 0u;
             const uint32_t idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(hw >> 3) << 17) |
                                    ((uint32_t)(kTileM >> 4) << 24);
-            const uint32_t a_addr = smem_u32(a_base);
             uint32_t it = 0, pa0 = 0, pa1 = 0;
             bool ok = true;
             for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
@@ -345,13 +432,12 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                                         tc_fence_after();
                                     }
                                     const uint64_t bd = smem_desc(b_addr + ks * 32);
-                                    const uint32_t a_off = (uint32_t)kb * 16384u + ks * 32;
-                                    const uint64_t ahi = smem_desc(a_addr + a_off);
+                                    const uint32_t acol = (uint32_t)g * 8u;  // 16 fp16 K-elements = 8 TMEM columns
                                     if (p == 0) {
-                                        mma_f16(d_addr, ahi, bd, idesc, g != 0);
-                                        if (PARTS == 2) mma_f16(d_addr, smem_desc(a_addr + P.a_part_bytes + a_off), bd, idesc, 1);
+                                        mma_ts(d_addr, a_hi + acol, bd, idesc, g != 0);
+                                        if (PARTS == 2) mma_ts(d_addr, a_lo + acol, bd, idesc, 1);
                                     } else {
-                                        mma_f16(d_addr, ahi, bd, idesc, 1);
+                                        mma_ts(d_addr, a_hi + acol, bd, idesc, 1);
                                     }
                                 }
                                 mma_commit(smem_u32(&empty_bar[s]));
@@ -373,48 +459,42 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
     } else {
         // ------------------------------------------------ epilogue warps 2..9
         const int q = warp & 3;                 // TMEM lane quadrant
-        const int grp = (warp - 2) >> 2;        // 0: units [0, W/2) (D0), 1: units [W/2, W) (D1)
+        const int w = (warp - 2) >> 2;          // which quarter of each N-half
         const int r = q * 32 + lane;            // tile row
-        const int et = threadIdx.x - 64;        // 0..255
-        const int j_begin = grp * hw;
-        const uint32_t t_lane = tmem + ((uint32_t)(q * 32) << 16);
-        const int gt = et & 127;                // thread index within the group
-        uint32_t pd = 0, pf = 0;                // phases of d_full[grp] and (group 0) a0_free
-        uint32_t px = 0;                        // phase of x_full (group 0) / x_empty (group 1)
-        bool pending_free = false;              // group 0: an a0_free phase not yet waited for
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        const uint32_t t_lane = tmem + lane_off;
+        const uint32_t a_hi_l = a_hi + lane_off, a_lo_l = a_lo + lane_off;
+        uint32_t pd0 = 0, pd1 = 0, pf = 0, px = 0;
+        bool pending_free = false;  // an a0_free phase not yet waited for
         bool ok = true;
-        // Tail exchange through two mbarriers (bounded waits, no cross-group named barrier):
-        // the D1 warps publish their partial dot products, the D0 warps add them to their own.
-        auto publish = [&](float sa, float sb) {
-            ok = mbar_wait(smem_u32(x_empty), px ^ 1, abort, hdr, 6, false) && ok;
-            px ^= 1;
-            tailx[r] = sa;
-            if (MULT) tailx[128 + r] = sb;
-            mbar_arrive(smem_u32(x_full));
-        };
-        auto collect = [&](float &sa, float &sb) {
-            ok = mbar_wait(smem_u32(x_full), px, abort, hdr, 7, false) && ok;
-            px ^= 1;
-            sa += tailx[r];
-            if (MULT) sb += tailx[128 + r];
-            mbar_arrive(smem_u32(x_empty));
-        };
-        auto group_sync = [&]() { named_sync(2 + grp, 128); };
-        auto wait_a_free = [&]() {
-            if (grp == 0 && pending_free) {
+        auto wait_free = [&]() {
+            if (pending_free) {
                 ok = mbar_wait(smem_u32(a0_free), pf, abort, hdr, 5, false) && ok;
                 pf ^= 1;
                 pending_free = false;
             }
         };
-        auto load_consts = [&](int l) {  // this group's columns of layer l's bias', tail a, tail b -> ring slot l & 1
-            float *dst = c_ring + (l & 1) * 3 * W;
-            const float *src = P.cvec + (size_t)(l - 1) * 3 * W;
-            if (gt < hw) {
-                const int j = j_begin + gt;
-                dst[j] = __ldg(src + j);
-                dst[W + j] = __ldg(src + W + j);
-                dst[2 * W + j] = __ldg(src + 2 * W + j);
+        auto signal_a = [&](int h) {  // this warp's part of A's K-half h is in TMEM
+            tmem_wait_st();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&a_ready[h]));
+        };
+        // Tail exchange through two mbarriers (bounded waits): warps 6-9 publish their
+        // partial dot products, warps 2-5 add them to their own.
+        auto exchange = [&](float &sa, float &sb) {
+            if (w == 1) {
+                ok = mbar_wait(smem_u32(x_empty), px ^ 1, abort, hdr, 6, false) && ok;
+                px ^= 1;
+                tailx[r] = sa;
+                if (MULT) tailx[128 + r] = sb;
+                mbar_arrive(smem_u32(x_full));
+            } else {
+                ok = mbar_wait(smem_u32(x_full), px, abort, hdr, 7, false) && ok;
+                px ^= 1;
+                sa += tailx[r];
+                if (MULT) sb += tailx[128 + r];
+                mbar_arrive(smem_u32(x_empty));
             }
         };
         for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
@@ -436,136 +516,126 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                 }
             }
             float y = 0.f;
-            if (Dt >= P.first_mma) load_consts(P.first_mma);
+            const bool write_first = Dt >= P.first_mma;
             // ---- layer 1 on the CUDA cores (or the Fourier features feeding an MMA layer 1)
             if (P.first_mma == 2) {
                 float ta = 0.f;
-                const bool write_a = Dt > 1;
-                if (write_a) wait_a_free();
-                for (int j0 = j_begin; j0 < j_begin + hw; j0 += 8) {
-                    float h8[8];
-                    const float4 w0a = *reinterpret_cast<const float4 *>(c_l1 + j0);
-                    const float4 w0b = *reinterpret_cast<const float4 *>(c_l1 + j0 + 4);
-                    const float4 w1a = *reinterpret_cast<const float4 *>(c_l1 + W + j0);
-                    const float4 w1b = *reinterpret_cast<const float4 *>(c_l1 + W + j0 + 4);
-                    const float4 w2a = *reinterpret_cast<const float4 *>(c_l1 + 2 * W + j0);
-                    const float4 w2b = *reinterpret_cast<const float4 *>(c_l1 + 2 * W + j0 + 4);
-                    const float4 ba = *reinterpret_cast<const float4 *>(c_l1 + 3 * W + j0);
-                    const float4 bb = *reinterpret_cast<const float4 *>(c_l1 + 3 * W + j0 + 4);
-                    const float4 aa = *reinterpret_cast<const float4 *>(c_l1 + 4 * W + j0);
-                    const float4 ab4 = *reinterpret_cast<const float4 *>(c_l1 + 4 * W + j0 + 4);
-                    const float w0v[8] = {w0a.x, w0a.y, w0a.z, w0a.w, w0b.x, w0b.y, w0b.z, w0b.w};
-                    const float w1v[8] = {w1a.x, w1a.y, w1a.z, w1a.w, w1b.x, w1b.y, w1b.z, w1b.w};
-                    const float w2v[8] = {w2a.x, w2a.y, w2a.z, w2a.w, w2b.x, w2b.y, w2b.z, w2b.w};
-                    const float bv[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
-                    const float av[8] = {aa.x, aa.y, aa.z, aa.w, ab4.x, ab4.y, ab4.z, ab4.w};
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        float u = fmaf(w0v[i], x0, bv[i]);
-                        u = fmaf(w1v[i], x1, u);
-                        u = fmaf(w2v[i], x2, u);
-                        const float hv = activate<ACT>(u);
-                        h8[i] = hv;
-                        ta = fmaf(av[i], hv, ta);
-                    }
-                    if (write_a) store_a8<MODE>(a_base, P.a_part_bytes, r, j0, h8);
-                }
-                if (write_a) {
-                    fence_async_smem();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(smem_u32(&a_ready[grp]));
-                }
-                if (grp == 1) {
-                    publish(ta, 0.f);
-                } else {
-                    float sb = 0.f;
-                    collect(ta, sb);
-                    y = ta + __ldg(P.tb);
-                    if (d == 1 && idx >= 0) out[idx] = y;
-                }
-                group_sync();  // this group's constants for the first tensor-core layer are visible
-            } else {
-                // Fourier features gamma(x) = [sin 2 pi s, cos 2 pi s] over this group's half of in_dim
-                const int hd = P.D >> 1;
-                wait_a_free();
-                for (int k0 = grp * hd; k0 < grp * hd + hd; k0 += 8) {
-                    float h8[8];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int k = k0 + i;
-                        const int kk = k < P.m ? k : k - P.m;
-                        const float ph = fourier_phase(P.B + 3 * kk, x0, x1, x2);
-                        float sv, cv;
-                        sincospif(2.0f * ph, &sv, &cv);
-                        h8[i] = k < P.m ? sv : cv;
-                    }
-                    store_a8<MODE>(a_base, P.a_part_bytes, r, k0, h8);
-                }
-                fence_async_smem();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&a_ready[grp]));
-                group_sync();  // this group's constants for the first tensor-core layer are visible
-            }
-            // ---- tensor-core layers
-            for (int l = P.first_mma; l <= Dt; ++l) {
-                ok = mbar_wait(smem_u32(&d_full[grp]), pd, abort, hdr, 4, false);
-                pd ^= 1;
-                if (!ok) break;
-                tc_fence_after();
-                if (grp == 0) pending_free = true;  // this layer's MMAs will release the first K-half of A
-                const bool last = l == Dt;
-                if (!last) load_consts(l + 1);
-                const float *cs = c_ring + (l & 1) * 3 * W;
-                const float c1 = P.c1[l - 1];
-                float sa = 0.f, sb = 0.f;
-                for (int c0 = j_begin; c0 < j_begin + hw; c0 += 32) {
-                    float v[32];
-                    tmem_ld32(t_lane + (uint32_t)c0, v);
-                    if (!last && c0 == j_begin) wait_a_free();
-#pragma unroll
-                    for (int g = 0; g < 4; ++g) {
-                        const int j0 = c0 + 8 * g;
-                        const float4 ba = *reinterpret_cast<const float4 *>(cs + j0);
-                        const float4 bb = *reinterpret_cast<const float4 *>(cs + j0 + 4);
-                        const float4 aa = *reinterpret_cast<const float4 *>(cs + W + j0);
-                        const float4 ab4 = *reinterpret_cast<const float4 *>(cs + W + j0 + 4);
+                const float *b1 = c_all;       // bias' of layer 1
+                const float *a1 = c_all + W;   // tail a of layer 1
+                for (int h = 0; h < 2; ++h) {
+                    const int u0 = h * hw + w * quarter;
+                    if (write_first && h == 0) wait_free();
+                    for (int c0 = u0; c0 < u0 + quarter; c0 += 8) {
+                        const float4 w0a = *reinterpret_cast<const float4 *>(c_l1 + c0);
+                        const float4 w0b = *reinterpret_cast<const float4 *>(c_l1 + c0 + 4);
+                        const float4 w1a = *reinterpret_cast<const float4 *>(c_l1 + W + c0);
+                        const float4 w1b = *reinterpret_cast<const float4 *>(c_l1 + W + c0 + 4);
+                        const float4 w2a = *reinterpret_cast<const float4 *>(c_l1 + 2 * W + c0);
+                        const float4 w2b = *reinterpret_cast<const float4 *>(c_l1 + 2 * W + c0 + 4);
+                        const float4 ba = *reinterpret_cast<const float4 *>(b1 + c0);
+                        const float4 bb = *reinterpret_cast<const float4 *>(b1 + c0 + 4);
+                        const float4 aa = *reinterpret_cast<const float4 *>(a1 + c0);
+                        const float4 ab4 = *reinterpret_cast<const float4 *>(a1 + c0 + 4);
+                        const float w0v[8] = {w0a.x, w0a.y, w0a.z, w0a.w, w0b.x, w0b.y, w0b.z, w0b.w};
+                        const float w1v[8] = {w1a.x, w1a.y, w1a.z, w1a.w, w1b.x, w1b.y, w1b.z, w1b.w};
+                        const float w2v[8] = {w2a.x, w2a.y, w2a.z, w2a.w, w2b.x, w2b.y, w2b.z, w2b.w};
                         const float bv[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
                         const float av[8] = {aa.x, aa.y, aa.z, aa.w, ab4.x, ab4.y, ab4.z, ab4.w};
-                        float tbv[8];
-                        if (MULT) {
-                            const float4 ta4 = *reinterpret_cast<const float4 *>(cs + 2 * W + j0);
-                            const float4 tb4 = *reinterpret_cast<const float4 *>(cs + 2 * W + j0 + 4);
-                            tbv[0] = ta4.x; tbv[1] = ta4.y; tbv[2] = ta4.z; tbv[3] = ta4.w;
-                            tbv[4] = tb4.x; tbv[5] = tb4.y; tbv[6] = tb4.z; tbv[7] = tb4.w;
-                        }
                         float h8[8];
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
-                            const float hv = activate<ACT>(fmaf(v[8 * g + i], c1, bv[i]));
+                            float u = fmaf(w0v[i], x0, bv[i]);
+                            u = fmaf(w1v[i], x1, u);
+                            u = fmaf(w2v[i], x2, u);
+                            const float hv = activate<ACT>(u);
                             h8[i] = hv;
-                            sa = fmaf(av[i], hv, sa);
-                            if (MULT) sb = fmaf(tbv[i], hv, sb);
+                            ta = fmaf(av[i], hv, ta);
                         }
-                        if (!last) store_a8<MODE>(a_base, P.a_part_bytes, r, j0, h8);
+                        if (write_first) {
+                            uint32_t phi[4], plo[4];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) pack2<MODE>(h8[2 * i], h8[2 * i + 1], phi[i], plo[i]);
+                            asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_hi_l + (uint32_t)(c0 >> 1)),
+                                         "r"(phi[0]), "r"(phi[1]), "r"(phi[2]), "r"(phi[3])
+                                         : "memory");
+                            if (MODE == TC_SPLIT16)
+                                asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_lo_l + (uint32_t)(c0 >> 1)),
+                                             "r"(plo[0]), "r"(plo[1]), "r"(plo[2]), "r"(plo[3])
+                                             : "memory");
+                        }
                     }
+                    if (write_first) signal_a(h);
                 }
-                tc_fence_before();
-                if (!last) {
-                    fence_async_smem();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(smem_u32(&a_ready[grp]));
+                float sb = 0.f;
+                exchange(ta, sb);
+                if (w == 0) {
+                    y = ta + __ldg(P.tb);
+                    if (d == 1 && idx >= 0) out[idx] = y;
                 }
-                if (grp == 1) {
-                    publish(sa, sb);
-                } else {
-                    collect(sa, sb);
+            } else {
+                // Fourier features gamma(x) = [sin 2 pi s, cos 2 pi s]; in_dim == W, same unit split as the layers
+                for (int h = 0; h < 2; ++h) {
+                    const int u0 = h * hw + w * quarter;
+                    if (h == 0) wait_free();
+                    for (int k0 = u0; k0 < u0 + quarter; k0 += 8) {
+                        float h8[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int k = k0 + i;
+                            const int kk = k < P.m ? k : k - P.m;
+                            const float ph = fourier_phase(P.B + 3 * kk, x0, x1, x2);
+                            float sv, cv;
+                            sincospif(2.0f * ph, &sv, &cv);
+                            h8[i] = k < P.m ? sv : cv;
+                        }
+                        uint32_t phi[4], plo[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) pack2<MODE>(h8[2 * i], h8[2 * i + 1], phi[i], plo[i]);
+                        asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_hi_l + (uint32_t)(k0 >> 1)),
+                                     "r"(phi[0]), "r"(phi[1]), "r"(phi[2]), "r"(phi[3])
+                                     : "memory");
+                        if (MODE == TC_SPLIT16)
+                            asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_lo_l + (uint32_t)(k0 >> 1)),
+                                         "r"(plo[0]), "r"(plo[1]), "r"(plo[2]), "r"(plo[3])
+                                         : "memory");
+                    }
+                    signal_a(h);
+                }
+            }
+            // ---- tensor-core layers
+            for (int l = P.first_mma; l <= Dt && ok; ++l) {
+                const bool last = l == Dt;
+                const float *cs = c_all + (size_t)(l - 1) * 3 * W;
+                const float c1 = P.c1[l - 1];
+                float sa = 0.f, sb = 0.f;
+                for (int h = 0; h < 2; ++h) {
+                    ok = mbar_wait(smem_u32(&d_full[h]), h == 0 ? pd0 : pd1, abort, hdr, 4, false) && ok;
+                    if (h == 0) pd0 ^= 1; else pd1 ^= 1;
+                    if (!ok) break;
+                    tc_fence_after();
+                    if (h == 0) pending_free = true;  // this layer's D1 MMAs will release the first K-half of A
+                    const int u0 = h * hw + w * quarter;
+                    if (quarter == 64)
+                        epilogue_half<MODE, ACT, TAIL, 32, 2>(P, cs, c1, t_lane, u0, !last, a_hi_l, a_lo_l, abort, hdr,
+                                                              a0_free, pf, pending_free, h == 0, sa, sb, ok);
+                    else if (quarter == 32)
+                        epilogue_half<MODE, ACT, TAIL, 32, 1>(P, cs, c1, t_lane, u0, !last, a_hi_l, a_lo_l, abort, hdr,
+                                                              a0_free, pf, pending_free, h == 0, sa, sb, ok);
+                    else
+                        epilogue_half<MODE, ACT, TAIL, 16, 1>(P, cs, c1, t_lane, u0, !last, a_hi_l, a_lo_l, abort, hdr,
+                                                              a0_free, pf, pending_free, h == 0, sa, sb, ok);
+                    if (!last) signal_a(h);
+                    else tc_fence_before();
+                }
+                if (!ok) break;
+                exchange(sa, sb);
+                if (w == 0) {
                     const float t0v = sa + __ldg(P.tb + 2 * (l - 1));
                     float tl = t0v;
                     if (MULT && l >= 2) tl = t0v * (sb + __ldg(P.tb + 2 * (l - 1) + 1));
                     y += tl;
                     if (d == l && idx >= 0) out[idx] = y;
                 }
-                group_sync();  // next layer's constants of this group are visible; this layer's slot is free
             }
         }
     }

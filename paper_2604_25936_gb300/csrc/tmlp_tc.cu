@@ -47,8 +47,9 @@ struct TcPack {
 };
 
 size_t tc_smem_bytes(const TcParams &P, int parts) {
-    return 1024 /*alignment slack*/ + (size_t)parts * P.a_part_bytes + (size_t)P.n_stages * P.stage_bytes +
-           (size_t)44 * P.W /*first-layer constants and the two-layer constant ring*/ + kMiscBytes;
+    (void)parts;  // the A operand lives in TMEM
+    return 1024 /*alignment slack*/ + (size_t)P.n_stages * P.stage_bytes +
+           (size_t)4 * (3 * P.W + (size_t)3 * P.L * P.W) /*first-layer weights, per-layer constants*/ + kMiscBytes;
 }
 
 sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params, int precision) {
@@ -179,8 +180,11 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
     P.first_mma = first;
     P.kpad = kpad;
     P.stage_bytes = (uint32_t)(W / 2) * 128u;
-    P.a_part_bytes = (uint32_t)kTileM * kpad * 2u;
-    P.tmem_cols = (uint32_t)W;
+    {   // accumulator (W columns) + A_hi (W/2) [+ A_lo (W/2)], rounded up to a power of two
+        uint32_t need = (uint32_t)W + (uint32_t)parts * (uint32_t)(W / 2), cols = 32;
+        while (cols < need) cols <<= 1;
+        P.tmem_cols = cols;
+    }
     for (int l = 0; l < kMaxLayers; ++l) P.c1[l] = c1[l];
     P.cvec = reinterpret_cast<const float *>(dbuf + off_c);
     P.w1p = reinterpret_cast<const float *>(dbuf + off_w1);
