@@ -1,26 +1,23 @@
 // Tensor-core T-MLP kernel for sm_103a (tcgen05 MMA, TMEM accumulators, TMA).
 //
 // Evaluates Eq. 2 (and Eq. 3 for multiplicative tails) for 128-row tiles of
-// points sorted by descending exit layer.  One persistent CTA per SM, 320 threads:
-//   warp 0      TMA producer: streams weight tiles (64 K-columns x W/2 units, one
-//               N-half of one K-block of one layer) from L2 into a ring of stages,
-//               128-byte swizzled (the K-major layout the MMA reads).
-//   warp 1      owns the TMEM accumulator (W fp32 columns) and issues tcgen05.mma
-//               from one thread.  Each layer is two accumulators, D0 = units
-//               [0, W/2) and D1 = [W/2, W), computed one after the other.
-//   warps 2..9  epilogue.  Thread (quadrant q, lane i) owns tile row 32 q + i (the
-//               TMEM lane restriction); warps 2-5 take the first quarter of the
-//               units of each N-half, warps 6-9 the second.  Layer 1 (float32, on
-//               the CUDA cores), bias, sine, tails, the running sum
-//               y_l = y_{l-1} + t_l and the write at each row's exit layer.  The new
-//               activations are packed to fp16 and written with tcgen05.st into
-//               TMEM, where the next layer's MMAs read them as the A operand.
-// TMEM columns: [0, W) accumulator (D0 | D1), then A_hi (W/2 columns of packed
-// fp16 pairs) and, in the float32 mode, A_lo.
-// Overlap: all epilogue warps turn D0 into activations while D1's MMAs run.  D1
-// reads the first K-half of A first and commits a barrier (a0_free) once it has,
-// so D0's results may replace that half; the next layer's MMAs on that K-half
-// start while D1's results are still being written.
+// points sorted by descending exit layer.  One persistent CTA per SM, 576 threads:
+//   warp 0       TMA producer: streams weight tiles (64 K-columns x W units, one
+//                K-block of one layer) from L2 into a ring of stages, 128-byte
+//                swizzled (the K-major layout the MMA reads).
+//   warp 1       owns TMEM and issues tcgen05.mma from one thread:
+//                D[128 x W] (fp32, TMEM) += A[128 x 16] . B[W x 16]^T, A read from TMEM.
+//   warps 2..17  epilogue.  Thread (quadrant q, lane i) owns tile row 32 q + i (the
+//                TMEM lane restriction); the four warps of a quadrant take a quarter
+//                of the units each.  Layer 1 (float32, on the CUDA cores), bias,
+//                sine, tails, the running sum y_l = y_{l-1} + t_l and the write at
+//                each row's exit layer.  The new activations are packed to fp16 and
+//                written with tcgen05.st into TMEM, where the next layer's MMAs read
+//                them as the A operand.
+// TMEM columns: [0, W) accumulator, then A_hi (W/2 columns of packed fp16 pairs)
+// and, in the float32 mode, A_lo.  One MMA stream at N = W: measured on GB300, one
+// issuing thread sustains about one M=128 MMA per 140-165 cycles whatever N is, so
+// N = 256 is what reaches the tensor cores' rate; layers run MMA then epilogue.
 // A tile runs to the exit layer of its first (deepest) row; rows whose exit layer
 // was reached ride along only in the one tile per exit layer that straddles two
 // layers; tiles of exit layer 1 never touch the tensor cores.
@@ -45,22 +42,24 @@ namespace sand {
 
 enum TcMode { TC_SPLIT16 = 0, TC_F16 = 1, TC_BF16 = 2 };
 
-constexpr int kTcThreads = 320;
+constexpr int kEpiWarps = 16;
+constexpr int kTcThreads = 64 + 32 * kEpiWarps;
 constexpr int kTileM = 128;
-constexpr int kEpiThreads = 256;
+constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 constexpr int kSmemBudget = 227 * 1024;
-constexpr int kMaxStages = 12;
-constexpr int kNumBars = 2 * kMaxStages + 8;  // full, empty, a_ready[2], d_full[2], a0_free, drain, x_full, x_empty
-// bytes after the weight stages and constants: barriers, TMEM slot + abort flag, tail exchange
-constexpr int kMiscBytes = kNumBars * 8 + 16 + 1024;
+constexpr int kMaxStages = 8;
+constexpr int kNumBars = 2 * kMaxStages + 5;  // full, empty, a_ready, d_full, drain, x_full, x_empty
+// bytes after the weight stages and constants: barriers, TMEM slot + abort flag,
+// tail exchange (3 slices x 2 values x 128 rows)
+constexpr int kMiscBytes = kNumBars * 8 + 16 + 3 * 2 * 128 * 4;
 
 struct TcParams {
     int L, W, D, tail_kind, act, enc, m;
     int first_mma;            // 1-based index of the first layer computed on the tensor cores
     int kpad;                 // padded K of the packed weight matrix (multiple of 64)
     int n_stages;
-    uint32_t stage_bytes;     // (W / 2) * 128
+    uint32_t stage_bytes;     // W * 128
     uint32_t tmem_cols;       // power of two >= W + parts * W / 2
     float c1[kMaxLayers];     // per layer: w0 / (2 pi s) (sine) or 1 / s (ReLU)
     const float *cvec;        // [L][3][W]: bias' (w0 b / 2 pi for sine, b for ReLU), tail a, tail b
@@ -244,60 +243,46 @@ __device__ __forceinline__ void tmem_st_half(uint32_t taddr, const uint32_t *v) 
 }
 
 // ------------------------------------------------------------------ the kernel
-// One N-half of a tensor-core layer for this thread's row: NCH chunks of CH accumulator
-// columns starting at unit u0 -> bias, activation, tail partial sums and (write_a) the
-// packed activations into TMEM as the next A operand.  Both chunks are loaded before one wait.
-template <int MODE, int ACT, int TAIL, int CH, int NCH>
-__device__ __forceinline__ void epilogue_half(const TcParams &P, const float *cs, float c1, uint32_t t_lane, int u0,
-                                              bool write_a, uint32_t a_hi, uint32_t a_lo, volatile int *abort,
-                                              WsHeader *hdr, uint64_t *a0_free, uint32_t &pf, bool &pending_free,
-                                              bool first_half, float &sa, float &sb, bool &ok) {
+// CH accumulator columns of this thread's row, starting at unit c0: bias, activation,
+// tail partial sums and, when write_a, the packed activations into TMEM (A operand).
+template <int MODE, int ACT, int TAIL, int CH>
+__device__ __forceinline__ void epilogue_chunk(const float *cs, int W, float c1, uint32_t t_lane, int c0, bool write_a,
+                                               uint32_t a_hi, uint32_t a_lo, float &sa, float &sb) {
     constexpr bool MULT = TAIL == SAND_TAIL_MULT;
-    const int W = P.W;
-    uint32_t v[NCH][CH];
-#pragma unroll
-    for (int ci = 0; ci < NCH; ++ci) tmem_ld_ch<CH>(t_lane + (uint32_t)(u0 + ci * CH), v[ci]);
+    uint32_t v[CH];
+    tmem_ld_ch<CH>(t_lane + (uint32_t)c0, v);
     tmem_wait_ld();
+    uint32_t phi[CH / 2], plo[CH / 2];
 #pragma unroll
-    for (int ci = 0; ci < NCH; ++ci) {
-        const int c0 = u0 + ci * CH;
-        uint32_t phi[CH / 2], plo[CH / 2];
-#pragma unroll
-        for (int g = 0; g < CH / 8; ++g) {
-            const int j0 = c0 + 8 * g;
-            const float4 ba = *reinterpret_cast<const float4 *>(cs + j0);
-            const float4 bb = *reinterpret_cast<const float4 *>(cs + j0 + 4);
-            const float4 aa = *reinterpret_cast<const float4 *>(cs + W + j0);
-            const float4 ab4 = *reinterpret_cast<const float4 *>(cs + W + j0 + 4);
-            const float bv[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
-            const float av[8] = {aa.x, aa.y, aa.z, aa.w, ab4.x, ab4.y, ab4.z, ab4.w};
-            float tbv[8];
-            if (MULT) {
-                const float4 t0 = *reinterpret_cast<const float4 *>(cs + 2 * W + j0);
-                const float4 t1 = *reinterpret_cast<const float4 *>(cs + 2 * W + j0 + 4);
-                tbv[0] = t0.x; tbv[1] = t0.y; tbv[2] = t0.z; tbv[3] = t0.w;
-                tbv[4] = t1.x; tbv[5] = t1.y; tbv[6] = t1.z; tbv[7] = t1.w;
-            }
-            float h8[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const float hv = activate<ACT>(fmaf(__uint_as_float(v[ci][8 * g + i]), c1, bv[i]));
-                h8[i] = hv;
-                sa = fmaf(av[i], hv, sa);
-                if (MULT) sb = fmaf(tbv[i], hv, sb);
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) pack2<MODE>(h8[2 * i], h8[2 * i + 1], phi[4 * g + i], plo[4 * g + i]);
+    for (int g = 0; g < CH / 8; ++g) {
+        const int j0 = c0 + 8 * g;
+        const float4 ba = *reinterpret_cast<const float4 *>(cs + j0);
+        const float4 bb = *reinterpret_cast<const float4 *>(cs + j0 + 4);
+        const float4 aa = *reinterpret_cast<const float4 *>(cs + W + j0);
+        const float4 ab4 = *reinterpret_cast<const float4 *>(cs + W + j0 + 4);
+        const float bv[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
+        const float av[8] = {aa.x, aa.y, aa.z, aa.w, ab4.x, ab4.y, ab4.z, ab4.w};
+        float tbv[8];
+        if (MULT) {
+            const float4 t0 = *reinterpret_cast<const float4 *>(cs + 2 * W + j0);
+            const float4 t1 = *reinterpret_cast<const float4 *>(cs + 2 * W + j0 + 4);
+            tbv[0] = t0.x; tbv[1] = t0.y; tbv[2] = t0.z; tbv[3] = t0.w;
+            tbv[4] = t1.x; tbv[5] = t1.y; tbv[6] = t1.z; tbv[7] = t1.w;
         }
-        if (write_a) {
-            if (first_half && pending_free) {  // D1's MMAs have read the first K-half of A
-                ok = mbar_wait(smem_u32(a0_free), pf, abort, hdr, 5, false) && ok;
-                pf ^= 1;
-                pending_free = false;
-            }
-            tmem_st_half<CH>(a_hi + (uint32_t)(c0 >> 1), phi);
-            if (MODE == TC_SPLIT16) tmem_st_half<CH>(a_lo + (uint32_t)(c0 >> 1), plo);
+        float h8[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float hv = activate<ACT>(fmaf(__uint_as_float(v[8 * g + i]), c1, bv[i]));
+            h8[i] = hv;
+            sa = fmaf(av[i], hv, sa);
+            if (MULT) sb = fmaf(tbv[i], hv, sb);
         }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) pack2<MODE>(h8[2 * i], h8[2 * i + 1], phi[4 * g + i], plo[4 * g + i]);
+    }
+    if (write_a) {
+        tmem_st_half<CH>(a_hi + (uint32_t)(c0 >> 1), phi);
+        if (MODE == TC_SPLIT16) tmem_st_half<CH>(a_lo + (uint32_t)(c0 >> 1), plo);
     }
 }
 
@@ -310,23 +295,21 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int W = P.W, L = P.L;
-    const int hw = W >> 1;
-    const int quarter = W >> 2;
+    const int quarter = W >> 2;  // units per epilogue slice
     uint8_t *stage_base = smem;
     float *c_l1 = reinterpret_cast<float *>(stage_base + (size_t)P.n_stages * P.stage_bytes);  // [3][W] first-layer weights
     float *c_all = c_l1 + 3 * W;                                                                // [L][3][W]
     uint64_t *bars = reinterpret_cast<uint64_t *>(c_all + (size_t)3 * L * W);
     uint64_t *full_bar = bars;
     uint64_t *empty_bar = bars + kMaxStages;
-    uint64_t *a_ready = bars + 2 * kMaxStages;  // [2]
-    uint64_t *d_full = a_ready + 2;             // [2]
-    uint64_t *a0_free = d_full + 2;
-    uint64_t *drain = a0_free + 1;
-    uint64_t *x_full = drain + 1;   // tail partials of warps 6-9 written (128 arrivals)
-    uint64_t *x_empty = x_full + 1; // ... and read by warps 2-5 (128 arrivals)
+    uint64_t *a_ready = bars + 2 * kMaxStages;  // the next A operand is in TMEM (one arrival per epilogue warp)
+    uint64_t *d_full = a_ready + 1;             // the layer's accumulator is complete
+    uint64_t *drain = d_full + 1;
+    uint64_t *x_full = drain + 1;   // tail partials of slices 1-3 written (384 arrivals)
+    uint64_t *x_empty = x_full + 1; // ... and read by slice 0 (128 arrivals)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + kNumBars);
     volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
-    float *tailx = reinterpret_cast<float *>(tmem_slot + 4);  // [2 values][128 rows]
+    float *tailx = reinterpret_cast<float *>(tmem_slot + 4);  // [3 slices][2 values][128 rows]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n_rows = full_depth ? n : (int64_t)hdr->n_active;
@@ -338,13 +321,10 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             mbar_init(smem_u32(&full_bar[s]), 1);
             mbar_init(smem_u32(&empty_bar[s]), 1);
         }
-        mbar_init(smem_u32(&a_ready[0]), 8);
-        mbar_init(smem_u32(&a_ready[1]), 8);
-        mbar_init(smem_u32(&d_full[0]), 1);
-        mbar_init(smem_u32(&d_full[1]), 1);
-        mbar_init(smem_u32(a0_free), 1);
+        mbar_init(smem_u32(a_ready), kEpiWarps);
+        mbar_init(smem_u32(d_full), 1);
         mbar_init(smem_u32(drain), 1);
-        mbar_init(smem_u32(x_full), 128);
+        mbar_init(smem_u32(x_full), 3 * 128);
         mbar_init(smem_u32(x_empty), 128);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -364,7 +344,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t a_hi = tmem + (uint32_t)W, a_lo = tmem + (uint32_t)(W + hw);
+    const uint32_t a_hi = tmem + (uint32_t)W, a_lo = tmem + (uint32_t)(W + W / 2);
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
@@ -375,16 +355,15 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                 const int Dt = tile_depth(t);
                 for (int l = P.first_mma; l <= Dt && ok; ++l) {
                     const int kb_n = (l == 1 ? P.D : W) >> 6;
-                    for (int h = 0; h < 2 && ok; ++h)
-                        for (int kb = 0; kb < kb_n && ok; ++kb)
-                            for (int p = 0; p < PARTS && ok; ++p, ++it) {
-                                const uint32_t s = it % P.n_stages, ph = (it / P.n_stages) & 1;
-                                ok = mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1, abort, hdr, 1, true);
-                                if (!ok) break;
-                                mbar_arrive_tx(smem_u32(&full_bar[s]), P.stage_bytes);
-                                tma_load_2d(smem_u32(stage_base + (size_t)s * P.stage_bytes), &wmap, smem_u32(&full_bar[s]),
-                                            kb * 64, ((l - P.first_mma) * PARTS + p) * W + h * hw);
-                            }
+                    for (int kb = 0; kb < kb_n && ok; ++kb)
+                        for (int p = 0; p < PARTS && ok; ++p, ++it) {
+                            const uint32_t s = it % P.n_stages, ph = (it / P.n_stages) & 1;
+                            ok = mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1, abort, hdr, 1, true);
+                            if (!ok) break;
+                            mbar_arrive_tx(smem_u32(&full_bar[s]), P.stage_bytes);
+                            tma_load_2d(smem_u32(stage_base + (size_t)s * P.stage_bytes), &wmap, smem_u32(&full_bar[s]),
+                                        kb * 64, ((l - P.first_mma) * PARTS + p) * W);
+                        }
                 }
             }
             if (!ok) {  // drain copies still in flight before the CTA can exit
@@ -401,51 +380,41 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t ab = MODE == TC_BF16 ? 1u : 0u;
-            const uint32_t idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(hw >> 3) << 17) |
+            const uint32_t idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(W >> 3) << 17) |
                                    ((uint32_t)(kTileM >> 4) << 24);
-            uint32_t it = 0, pa0 = 0, pa1 = 0;
+            uint32_t it = 0, pa = 0;
             bool ok = true;
             for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
                 const int Dt = tile_depth(t);
                 for (int l = P.first_mma; l <= Dt && ok; ++l) {
-                    const int K = l == 1 ? P.D : W;
-                    const int kb_n = K >> 6;
-                    const int g_half = K >> 5;  // first K-step (of 16) in the second half of A
-                    const int kb_last_first_half = (g_half - 1) >> 2;
-                    for (int h = 0; h < 2 && ok; ++h) {
-                        const uint32_t d_addr = tmem + (uint32_t)(h * hw);
-                        for (int kb = 0; kb < kb_n && ok; ++kb) {
-                            for (int p = 0; p < PARTS && ok; ++p, ++it) {
-                                const uint32_t s = it % P.n_stages, ph = (it / P.n_stages) & 1;
-                                ok = mbar_wait(smem_u32(&full_bar[s]), ph, abort, hdr, 3, true);
-                                if (!ok) break;
-                                tc_fence_after();
-                                const uint32_t b_addr = smem_u32(stage_base + (size_t)s * P.stage_bytes);
+                    ok = mbar_wait(smem_u32(a_ready), pa, abort, hdr, 2, true);
+                    pa ^= 1;
+                    if (!ok) break;
+                    tc_fence_after();
+                    const int kb_n = (l == 1 ? P.D : W) >> 6;
+                    for (int kb = 0; kb < kb_n && ok; ++kb) {
+                        for (int p = 0; p < PARTS && ok; ++p, ++it) {
+                            const uint32_t s = it % P.n_stages, ph = (it / P.n_stages) & 1;
+                            ok = mbar_wait(smem_u32(&full_bar[s]), ph, abort, hdr, 3, true);
+                            if (!ok) break;
+                            tc_fence_after();
+                            const uint32_t b_addr = smem_u32(stage_base + (size_t)s * P.stage_bytes);
 #pragma unroll
-                                for (int ks = 0; ks < 4; ++ks) {
-                                    const int g = kb * 4 + ks;
-                                    if (h == 0 && p == 0 && (g == 0 || g == g_half)) {
-                                        uint32_t &pr = g == 0 ? pa0 : pa1;
-                                        ok = mbar_wait(smem_u32(&a_ready[g == 0 ? 0 : 1]), pr, abort, hdr, 2, true);
-                                        pr ^= 1;
-                                        if (!ok) break;
-                                        tc_fence_after();
-                                    }
-                                    const uint64_t bd = smem_desc(b_addr + ks * 32);
-                                    const uint32_t acol = (uint32_t)g * 8u;  // 16 fp16 K-elements = 8 TMEM columns
-                                    if (p == 0) {
-                                        mma_ts(d_addr, a_hi + acol, bd, idesc, g != 0);
-                                        if (PARTS == 2) mma_ts(d_addr, a_lo + acol, bd, idesc, 1);
-                                    } else {
-                                        mma_ts(d_addr, a_hi + acol, bd, idesc, 1);
-                                    }
+                            for (int ks = 0; ks < 4; ++ks) {
+                                const int g = kb * 4 + ks;
+                                const uint64_t bd = smem_desc(b_addr + ks * 32);
+                                const uint32_t acol = (uint32_t)g * 8u;  // 16 fp16 K-elements = 8 TMEM columns
+                                if (p == 0) {
+                                    mma_ts(tmem, a_hi + acol, bd, idesc, g != 0);
+                                    if (PARTS == 2) mma_ts(tmem, a_lo + acol, bd, idesc, 1);
+                                } else {
+                                    mma_ts(tmem, a_hi + acol, bd, idesc, 1);
                                 }
-                                mma_commit(smem_u32(&empty_bar[s]));
-                                if (h == 1 && p == PARTS - 1 && kb == kb_last_first_half) mma_commit(smem_u32(a0_free));
                             }
+                            mma_commit(smem_u32(&empty_bar[s]));
                         }
-                        if (ok) mma_commit(smem_u32(&d_full[h]));
                     }
+                    if (ok) mma_commit(smem_u32(d_full));
                 }
             }
             if (!ok) {  // let every issued MMA finish before TMEM is released
@@ -457,45 +426,53 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
         }
         __syncwarp();
     } else {
-        // ------------------------------------------------ epilogue warps 2..9
+        // ------------------------------------------------ epilogue warps 2..17
         const int q = warp & 3;                 // TMEM lane quadrant
-        const int w = (warp - 2) >> 2;          // which quarter of each N-half
+        const int slice = (warp - 2) >> 2;      // which quarter of the units
         const int r = q * 32 + lane;            // tile row
+        const int u0 = slice * quarter;
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
         const uint32_t t_lane = tmem + lane_off;
         const uint32_t a_hi_l = a_hi + lane_off, a_lo_l = a_lo + lane_off;
-        uint32_t pd0 = 0, pd1 = 0, pf = 0, px = 0;
-        bool pending_free = false;  // an a0_free phase not yet waited for
+        uint32_t pd = 0, px = 0;
         bool ok = true;
-        auto wait_free = [&]() {
-            if (pending_free) {
-                ok = mbar_wait(smem_u32(a0_free), pf, abort, hdr, 5, false) && ok;
-                pf ^= 1;
-                pending_free = false;
-            }
-        };
-        auto signal_a = [&](int h) {  // this warp's part of A's K-half h is in TMEM
+        auto signal_a = [&]() {  // this warp's part of the next A operand is in TMEM
             tmem_wait_st();
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&a_ready[h]));
+            if (lane == 0) mbar_arrive(smem_u32(a_ready));
         };
-        // Tail exchange through two mbarriers (bounded waits): warps 6-9 publish their
-        // partial dot products, warps 2-5 add them to their own.
+        // Tail exchange through two mbarriers (bounded waits): slices 1-3 publish their
+        // partial dot products, slice 0 adds them to its own.
         auto exchange = [&](float &sa, float &sb) {
-            if (w == 1) {
+            if (slice != 0) {
                 ok = mbar_wait(smem_u32(x_empty), px ^ 1, abort, hdr, 6, false) && ok;
                 px ^= 1;
-                tailx[r] = sa;
-                if (MULT) tailx[128 + r] = sb;
+                tailx[(slice - 1) * 256 + r] = sa;
+                if (MULT) tailx[(slice - 1) * 256 + 128 + r] = sb;
                 mbar_arrive(smem_u32(x_full));
             } else {
                 ok = mbar_wait(smem_u32(x_full), px, abort, hdr, 7, false) && ok;
                 px ^= 1;
-                sa += tailx[r];
-                if (MULT) sb += tailx[128 + r];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    sa += tailx[k * 256 + r];
+                    if (MULT) sb += tailx[k * 256 + 128 + r];
+                }
                 mbar_arrive(smem_u32(x_empty));
             }
+        };
+        auto st_a8 = [&](int c0, const float *h8) {  // 8 activations of units c0..c0+7 into TMEM
+            uint32_t phi[4], plo[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) pack2<MODE>(h8[2 * i], h8[2 * i + 1], phi[i], plo[i]);
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_hi_l + (uint32_t)(c0 >> 1)),
+                         "r"(phi[0]), "r"(phi[1]), "r"(phi[2]), "r"(phi[3])
+                         : "memory");
+            if (MODE == TC_SPLIT16)
+                asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_lo_l + (uint32_t)(c0 >> 1)),
+                             "r"(plo[0]), "r"(plo[1]), "r"(plo[2]), "r"(plo[3])
+                             : "memory");
         };
         for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
             const int Dt = tile_depth(t);
@@ -522,114 +499,78 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                 float ta = 0.f;
                 const float *b1 = c_all;       // bias' of layer 1
                 const float *a1 = c_all + W;   // tail a of layer 1
-                for (int h = 0; h < 2; ++h) {
-                    const int u0 = h * hw + w * quarter;
-                    if (write_first && h == 0) wait_free();
-                    for (int c0 = u0; c0 < u0 + quarter; c0 += 8) {
-                        const float4 w0a = *reinterpret_cast<const float4 *>(c_l1 + c0);
-                        const float4 w0b = *reinterpret_cast<const float4 *>(c_l1 + c0 + 4);
-                        const float4 w1a = *reinterpret_cast<const float4 *>(c_l1 + W + c0);
-                        const float4 w1b = *reinterpret_cast<const float4 *>(c_l1 + W + c0 + 4);
-                        const float4 w2a = *reinterpret_cast<const float4 *>(c_l1 + 2 * W + c0);
-                        const float4 w2b = *reinterpret_cast<const float4 *>(c_l1 + 2 * W + c0 + 4);
-                        const float4 ba = *reinterpret_cast<const float4 *>(b1 + c0);
-                        const float4 bb = *reinterpret_cast<const float4 *>(b1 + c0 + 4);
-                        const float4 aa = *reinterpret_cast<const float4 *>(a1 + c0);
-                        const float4 ab4 = *reinterpret_cast<const float4 *>(a1 + c0 + 4);
-                        const float w0v[8] = {w0a.x, w0a.y, w0a.z, w0a.w, w0b.x, w0b.y, w0b.z, w0b.w};
-                        const float w1v[8] = {w1a.x, w1a.y, w1a.z, w1a.w, w1b.x, w1b.y, w1b.z, w1b.w};
-                        const float w2v[8] = {w2a.x, w2a.y, w2a.z, w2a.w, w2b.x, w2b.y, w2b.z, w2b.w};
-                        const float bv[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
-                        const float av[8] = {aa.x, aa.y, aa.z, aa.w, ab4.x, ab4.y, ab4.z, ab4.w};
-                        float h8[8];
+                for (int c0 = u0; c0 < u0 + quarter; c0 += 8) {
+                    const float4 w0a = *reinterpret_cast<const float4 *>(c_l1 + c0);
+                    const float4 w0b = *reinterpret_cast<const float4 *>(c_l1 + c0 + 4);
+                    const float4 w1a = *reinterpret_cast<const float4 *>(c_l1 + W + c0);
+                    const float4 w1b = *reinterpret_cast<const float4 *>(c_l1 + W + c0 + 4);
+                    const float4 w2a = *reinterpret_cast<const float4 *>(c_l1 + 2 * W + c0);
+                    const float4 w2b = *reinterpret_cast<const float4 *>(c_l1 + 2 * W + c0 + 4);
+                    const float4 ba = *reinterpret_cast<const float4 *>(b1 + c0);
+                    const float4 bb = *reinterpret_cast<const float4 *>(b1 + c0 + 4);
+                    const float4 aa = *reinterpret_cast<const float4 *>(a1 + c0);
+                    const float4 ab4 = *reinterpret_cast<const float4 *>(a1 + c0 + 4);
+                    const float w0v[8] = {w0a.x, w0a.y, w0a.z, w0a.w, w0b.x, w0b.y, w0b.z, w0b.w};
+                    const float w1v[8] = {w1a.x, w1a.y, w1a.z, w1a.w, w1b.x, w1b.y, w1b.z, w1b.w};
+                    const float w2v[8] = {w2a.x, w2a.y, w2a.z, w2a.w, w2b.x, w2b.y, w2b.z, w2b.w};
+                    const float bv[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
+                    const float av[8] = {aa.x, aa.y, aa.z, aa.w, ab4.x, ab4.y, ab4.z, ab4.w};
+                    float h8[8];
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            float u = fmaf(w0v[i], x0, bv[i]);
-                            u = fmaf(w1v[i], x1, u);
-                            u = fmaf(w2v[i], x2, u);
-                            const float hv = activate<ACT>(u);
-                            h8[i] = hv;
-                            ta = fmaf(av[i], hv, ta);
-                        }
-                        if (write_first) {
-                            uint32_t phi[4], plo[4];
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) pack2<MODE>(h8[2 * i], h8[2 * i + 1], phi[i], plo[i]);
-                            asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_hi_l + (uint32_t)(c0 >> 1)),
-                                         "r"(phi[0]), "r"(phi[1]), "r"(phi[2]), "r"(phi[3])
-                                         : "memory");
-                            if (MODE == TC_SPLIT16)
-                                asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_lo_l + (uint32_t)(c0 >> 1)),
-                                             "r"(plo[0]), "r"(plo[1]), "r"(plo[2]), "r"(plo[3])
-                                             : "memory");
-                        }
+                    for (int i = 0; i < 8; ++i) {
+                        float u = fmaf(w0v[i], x0, bv[i]);
+                        u = fmaf(w1v[i], x1, u);
+                        u = fmaf(w2v[i], x2, u);
+                        const float hv = activate<ACT>(u);
+                        h8[i] = hv;
+                        ta = fmaf(av[i], hv, ta);
                     }
-                    if (write_first) signal_a(h);
+                    if (write_first) st_a8(c0, h8);
                 }
+                if (write_first) signal_a();
                 float sb = 0.f;
                 exchange(ta, sb);
-                if (w == 0) {
+                if (slice == 0) {
                     y = ta + __ldg(P.tb);
                     if (d == 1 && idx >= 0) out[idx] = y;
                 }
             } else {
-                // Fourier features gamma(x) = [sin 2 pi s, cos 2 pi s]; in_dim == W, same unit split as the layers
-                for (int h = 0; h < 2; ++h) {
-                    const int u0 = h * hw + w * quarter;
-                    if (h == 0) wait_free();
-                    for (int k0 = u0; k0 < u0 + quarter; k0 += 8) {
-                        float h8[8];
+                // Fourier features gamma(x) = [sin 2 pi s, cos 2 pi s]; in_dim == W, same unit slices as the layers
+                for (int k0 = u0; k0 < u0 + quarter; k0 += 8) {
+                    float h8[8];
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const int k = k0 + i;
-                            const int kk = k < P.m ? k : k - P.m;
-                            const float ph = fourier_phase(P.B + 3 * kk, x0, x1, x2);
-                            float sv, cv;
-                            sincospif(2.0f * ph, &sv, &cv);
-                            h8[i] = k < P.m ? sv : cv;
-                        }
-                        uint32_t phi[4], plo[4];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) pack2<MODE>(h8[2 * i], h8[2 * i + 1], phi[i], plo[i]);
-                        asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_hi_l + (uint32_t)(k0 >> 1)),
-                                     "r"(phi[0]), "r"(phi[1]), "r"(phi[2]), "r"(phi[3])
-                                     : "memory");
-                        if (MODE == TC_SPLIT16)
-                            asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_lo_l + (uint32_t)(k0 >> 1)),
-                                         "r"(plo[0]), "r"(plo[1]), "r"(plo[2]), "r"(plo[3])
-                                         : "memory");
+                    for (int i = 0; i < 8; ++i) {
+                        const int k = k0 + i;
+                        const int kk = k < P.m ? k : k - P.m;
+                        const float ph = fourier_phase(P.B + 3 * kk, x0, x1, x2);
+                        float sv, cv;
+                        sincospif(2.0f * ph, &sv, &cv);
+                        h8[i] = k < P.m ? sv : cv;
                     }
-                    signal_a(h);
+                    st_a8(k0, h8);
                 }
+                signal_a();
             }
             // ---- tensor-core layers
             for (int l = P.first_mma; l <= Dt && ok; ++l) {
+                ok = mbar_wait(smem_u32(d_full), pd, abort, hdr, 4, false) && ok;
+                pd ^= 1;
+                if (!ok) break;
+                tc_fence_after();
                 const bool last = l == Dt;
                 const float *cs = c_all + (size_t)(l - 1) * 3 * W;
                 const float c1 = P.c1[l - 1];
                 float sa = 0.f, sb = 0.f;
-                for (int h = 0; h < 2; ++h) {
-                    ok = mbar_wait(smem_u32(&d_full[h]), h == 0 ? pd0 : pd1, abort, hdr, 4, false) && ok;
-                    if (h == 0) pd0 ^= 1; else pd1 ^= 1;
-                    if (!ok) break;
-                    tc_fence_after();
-                    if (h == 0) pending_free = true;  // this layer's D1 MMAs will release the first K-half of A
-                    const int u0 = h * hw + w * quarter;
-                    if (quarter == 64)
-                        epilogue_half<MODE, ACT, TAIL, 32, 2>(P, cs, c1, t_lane, u0, !last, a_hi_l, a_lo_l, abort, hdr,
-                                                              a0_free, pf, pending_free, h == 0, sa, sb, ok);
-                    else if (quarter == 32)
-                        epilogue_half<MODE, ACT, TAIL, 32, 1>(P, cs, c1, t_lane, u0, !last, a_hi_l, a_lo_l, abort, hdr,
-                                                              a0_free, pf, pending_free, h == 0, sa, sb, ok);
-                    else
-                        epilogue_half<MODE, ACT, TAIL, 16, 1>(P, cs, c1, t_lane, u0, !last, a_hi_l, a_lo_l, abort, hdr,
-                                                              a0_free, pf, pending_free, h == 0, sa, sb, ok);
-                    if (!last) signal_a(h);
-                    else tc_fence_before();
+                if (quarter >= 32) {
+                    for (int c0 = u0; c0 < u0 + quarter; c0 += 32)
+                        epilogue_chunk<MODE, ACT, TAIL, 32>(cs, W, c1, t_lane, c0, !last, a_hi_l, a_lo_l, sa, sb);
+                } else {
+                    epilogue_chunk<MODE, ACT, TAIL, 16>(cs, W, c1, t_lane, u0, !last, a_hi_l, a_lo_l, sa, sb);
                 }
-                if (!ok) break;
+                if (!last) signal_a();
+                else tc_fence_before();
                 exchange(sa, sb);
-                if (w == 0) {
+                if (slice == 0) {
                     const float t0v = sa + __ldg(P.tb + 2 * (l - 1));
                     float tl = t0v;
                     if (MULT && l >= 2) tl = t0v * (sb + __ldg(P.tb + 2 * (l - 1) + 1));

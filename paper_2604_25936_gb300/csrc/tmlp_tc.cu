@@ -164,7 +164,7 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
     }
     cuuint64_t gdim[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
     cuuint64_t gstride[1] = {(cuuint64_t)kpad * 2};
-    cuuint32_t box[2] = {64, (cuuint32_t)(W / 2)};
+    cuuint32_t box[2] = {64, (cuuint32_t)W};
     cuuint32_t estride[2] = {1, 1};
     CUresult cr = enc(&pk->map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, dbuf, gdim, gstride, box, estride,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -179,7 +179,7 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
     P.L = L; P.W = W; P.D = D; P.tail_kind = d.tail_kind; P.act = d.activation; P.enc = d.encoder; P.m = mf;
     P.first_mma = first;
     P.kpad = kpad;
-    P.stage_bytes = (uint32_t)(W / 2) * 128u;
+    P.stage_bytes = (uint32_t)W * 128u;
     {   // accumulator (W columns) + A_hi (W/2) [+ A_lo (W/2)], rounded up to a power of two
         uint32_t need = (uint32_t)W + (uint32_t)parts * (uint32_t)(W / 2), cols = 32;
         while (cols < need) cols <<= 1;
