@@ -17,7 +17,13 @@
 // TMEM columns: [0, W) accumulator, then A_hi (W/2 columns of packed fp16 pairs)
 // and, in the float32 mode, A_lo.  One MMA stream at N = W: measured on GB300, one
 // issuing thread sustains about one M=128 MMA per 140-165 cycles whatever N is, so
-// N = 256 is what reaches the tensor cores' rate; layers run MMA then epilogue.
+// N = 256 is what reaches the tensor cores' rate.
+// Overlap of a layer's epilogue with the next layer's MMAs: each epilogue thread
+// first loads all of its accumulator columns into registers and signals d_drained
+// (the next layer may now overwrite D), then produces the next A operand one
+// K-block (64 units) at a time, signalling a_ready[kb] after each; the MMAs of the
+// next layer on K-block kb start as soon as a_ready[kb] completes.  Thread
+// (quadrant, slice s) owns units 64 kb + 16 s .. + 15 of every K-block kb.
 // A tile runs to the exit layer of its first (deepest) row; rows whose exit layer
 // was reached ride along only in the one tile per exit layer that straddles two
 // layers; tiles of exit layer 1 never touch the tensor cores.
@@ -49,7 +55,8 @@ constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 constexpr int kSmemBudget = 227 * 1024;
 constexpr int kMaxStages = 8;
-constexpr int kNumBars = 2 * kMaxStages + 5;  // full, empty, a_ready, d_full, drain, x_full, x_empty
+constexpr int kMaxKBlocks = 4;  // W <= 256
+constexpr int kNumBars = 2 * kMaxStages + kMaxKBlocks + 5;  // full, empty, a_ready[kb], d_full, d_drained, drain, x_full, x_empty
 // bytes after the weight stages and constants: barriers, TMEM slot + abort flag,
 // tail exchange (3 slices x 2 values x 128 rows)
 constexpr int kMiscBytes = kNumBars * 8 + 16 + 3 * 2 * 128 * 4;
@@ -243,18 +250,15 @@ __device__ __forceinline__ void tmem_st_half(uint32_t taddr, const uint32_t *v) 
 }
 
 // ------------------------------------------------------------------ the kernel
-// CH accumulator columns of this thread's row, starting at unit c0: bias, activation,
+// 16 accumulator values (units c0 .. c0+15) of this thread's row: bias, activation,
 // tail partial sums and, when write_a, the packed activations into TMEM (A operand).
-template <int MODE, int ACT, int TAIL, int CH>
-__device__ __forceinline__ void epilogue_chunk(const float *cs, int W, float c1, uint32_t t_lane, int c0, bool write_a,
-                                               uint32_t a_hi, uint32_t a_lo, float &sa, float &sb) {
+template <int MODE, int ACT, int TAIL>
+__device__ __forceinline__ void epilogue16(const float *cs, int W, float c1, const uint32_t *v, int c0, bool write_a,
+                                           uint32_t a_hi, uint32_t a_lo, float &sa, float &sb) {
     constexpr bool MULT = TAIL == SAND_TAIL_MULT;
-    uint32_t v[CH];
-    tmem_ld_ch<CH>(t_lane + (uint32_t)c0, v);
-    tmem_wait_ld();
-    uint32_t phi[CH / 2], plo[CH / 2];
+    uint32_t phi[8], plo[8];
 #pragma unroll
-    for (int g = 0; g < CH / 8; ++g) {
+    for (int g = 0; g < 2; ++g) {
         const int j0 = c0 + 8 * g;
         const float4 ba = *reinterpret_cast<const float4 *>(cs + j0);
         const float4 bb = *reinterpret_cast<const float4 *>(cs + j0 + 4);
@@ -281,8 +285,8 @@ __device__ __forceinline__ void epilogue_chunk(const float *cs, int W, float c1,
         for (int i = 0; i < 4; ++i) pack2<MODE>(h8[2 * i], h8[2 * i + 1], phi[4 * g + i], plo[4 * g + i]);
     }
     if (write_a) {
-        tmem_st_half<CH>(a_hi + (uint32_t)(c0 >> 1), phi);
-        if (MODE == TC_SPLIT16) tmem_st_half<CH>(a_lo + (uint32_t)(c0 >> 1), plo);
+        tmem_st8(a_hi + (uint32_t)(c0 >> 1), phi);
+        if (MODE == TC_SPLIT16) tmem_st8(a_lo + (uint32_t)(c0 >> 1), plo);
     }
 }
 
@@ -295,16 +299,18 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int W = P.W, L = P.L;
-    const int quarter = W >> 2;  // units per epilogue slice
+    const int KB = W >> 6;  // K-blocks of 64 units
     uint8_t *stage_base = smem;
-    float *c_l1 = reinterpret_cast<float *>(stage_base + (size_t)P.n_stages * P.stage_bytes);  // [3][W] first-layer weights
+    float *dbuf = reinterpret_cast<float *>(stage_base + (size_t)P.n_stages * P.stage_bytes);  // [(KB-2)*16][512]
+    float *c_l1 = dbuf + (size_t)(KB > 2 ? KB - 2 : 0) * 16 * kEpiThreads;                     // [3][W] first-layer weights
     float *c_all = c_l1 + 3 * W;                                                                // [L][3][W]
     uint64_t *bars = reinterpret_cast<uint64_t *>(c_all + (size_t)3 * L * W);
     uint64_t *full_bar = bars;
     uint64_t *empty_bar = bars + kMaxStages;
-    uint64_t *a_ready = bars + 2 * kMaxStages;  // the next A operand is in TMEM (one arrival per epilogue warp)
-    uint64_t *d_full = a_ready + 1;             // the layer's accumulator is complete
-    uint64_t *drain = d_full + 1;
+    uint64_t *a_ready = bars + 2 * kMaxStages;  // [kb]: K-block kb of the next A operand is in TMEM (16 warps)
+    uint64_t *d_full = a_ready + kMaxKBlocks;   // the layer's accumulator is complete
+    uint64_t *d_drained = d_full + 1;           // every epilogue warp has read the accumulator (16 warps)
+    uint64_t *drain = d_drained + 1;
     uint64_t *x_full = drain + 1;   // tail partials of slices 1-3 written (384 arrivals)
     uint64_t *x_empty = x_full + 1; // ... and read by slice 0 (128 arrivals)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + kNumBars);
@@ -321,8 +327,9 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             mbar_init(smem_u32(&full_bar[s]), 1);
             mbar_init(smem_u32(&empty_bar[s]), 1);
         }
-        mbar_init(smem_u32(a_ready), kEpiWarps);
+        for (int kb = 0; kb < kMaxKBlocks; ++kb) mbar_init(smem_u32(&a_ready[kb]), kEpiWarps);
         mbar_init(smem_u32(d_full), 1);
+        mbar_init(smem_u32(d_drained), kEpiWarps);
         mbar_init(smem_u32(drain), 1);
         mbar_init(smem_u32(x_full), 3 * 128);
         mbar_init(smem_u32(x_empty), 128);
@@ -382,17 +389,24 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             const uint32_t ab = MODE == TC_BF16 ? 1u : 0u;
             const uint32_t idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(W >> 3) << 17) |
                                    ((uint32_t)(kTileM >> 4) << 24);
-            uint32_t it = 0, pa = 0;
-            bool ok = true;
+            uint32_t it = 0, pdr = 0;
+            uint32_t pa[kMaxKBlocks] = {0, 0, 0, 0};
+            bool ok = true, any_layer = false;
             for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
                 const int Dt = tile_depth(t);
                 for (int l = P.first_mma; l <= Dt && ok; ++l) {
-                    ok = mbar_wait(smem_u32(a_ready), pa, abort, hdr, 2, true);
-                    pa ^= 1;
-                    if (!ok) break;
-                    tc_fence_after();
+                    if (any_layer) {  // the previous layer's accumulator has been read out
+                        ok = mbar_wait(smem_u32(d_drained), pdr, abort, hdr, 8, true);
+                        pdr ^= 1;
+                        if (!ok) break;
+                    }
+                    any_layer = true;
                     const int kb_n = (l == 1 ? P.D : W) >> 6;
                     for (int kb = 0; kb < kb_n && ok; ++kb) {
+                        ok = mbar_wait(smem_u32(&a_ready[kb]), pa[kb], abort, hdr, 2, true);
+                        pa[kb] ^= 1;
+                        if (!ok) break;
+                        tc_fence_after();
                         for (int p = 0; p < PARTS && ok; ++p, ++it) {
                             const uint32_t s = it % P.n_stages, ph = (it / P.n_stages) & 1;
                             ok = mbar_wait(smem_u32(&full_bar[s]), ph, abort, hdr, 3, true);
@@ -428,19 +442,18 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
     } else {
         // ------------------------------------------------ epilogue warps 2..17
         const int q = warp & 3;                 // TMEM lane quadrant
-        const int slice = (warp - 2) >> 2;      // which quarter of the units
+        const int slice = (warp - 2) >> 2;      // 16-unit slice of every K-block
         const int r = q * 32 + lane;            // tile row
-        const int u0 = slice * quarter;
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
         const uint32_t t_lane = tmem + lane_off;
         const uint32_t a_hi_l = a_hi + lane_off, a_lo_l = a_lo + lane_off;
         uint32_t pd = 0, px = 0;
         bool ok = true;
-        auto signal_a = [&]() {  // this warp's part of the next A operand is in TMEM
-            tmem_wait_st();
+        auto signal = [&](uint64_t *bar, bool after_st) {  // this warp's share is done
+            if (after_st) tmem_wait_st();
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(a_ready));
+            if (lane == 0) mbar_arrive(smem_u32(bar));
         };
         // Tail exchange through two mbarriers (bounded waits): slices 1-3 publish their
         // partial dot products, slice 0 adds them to its own.
@@ -499,35 +512,37 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                 float ta = 0.f;
                 const float *b1 = c_all;       // bias' of layer 1
                 const float *a1 = c_all + W;   // tail a of layer 1
-                for (int c0 = u0; c0 < u0 + quarter; c0 += 8) {
-                    const float4 w0a = *reinterpret_cast<const float4 *>(c_l1 + c0);
-                    const float4 w0b = *reinterpret_cast<const float4 *>(c_l1 + c0 + 4);
-                    const float4 w1a = *reinterpret_cast<const float4 *>(c_l1 + W + c0);
-                    const float4 w1b = *reinterpret_cast<const float4 *>(c_l1 + W + c0 + 4);
-                    const float4 w2a = *reinterpret_cast<const float4 *>(c_l1 + 2 * W + c0);
-                    const float4 w2b = *reinterpret_cast<const float4 *>(c_l1 + 2 * W + c0 + 4);
-                    const float4 ba = *reinterpret_cast<const float4 *>(b1 + c0);
-                    const float4 bb = *reinterpret_cast<const float4 *>(b1 + c0 + 4);
-                    const float4 aa = *reinterpret_cast<const float4 *>(a1 + c0);
-                    const float4 ab4 = *reinterpret_cast<const float4 *>(a1 + c0 + 4);
-                    const float w0v[8] = {w0a.x, w0a.y, w0a.z, w0a.w, w0b.x, w0b.y, w0b.z, w0b.w};
-                    const float w1v[8] = {w1a.x, w1a.y, w1a.z, w1a.w, w1b.x, w1b.y, w1b.z, w1b.w};
-                    const float w2v[8] = {w2a.x, w2a.y, w2a.z, w2a.w, w2b.x, w2b.y, w2b.z, w2b.w};
-                    const float bv[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
-                    const float av[8] = {aa.x, aa.y, aa.z, aa.w, ab4.x, ab4.y, ab4.z, ab4.w};
-                    float h8[8];
+                for (int kb = 0; kb < KB; ++kb) {
+                    for (int c0 = 64 * kb + 16 * slice; c0 < 64 * kb + 16 * slice + 16; c0 += 8) {
+                        const float4 w0a = *reinterpret_cast<const float4 *>(c_l1 + c0);
+                        const float4 w0b = *reinterpret_cast<const float4 *>(c_l1 + c0 + 4);
+                        const float4 w1a = *reinterpret_cast<const float4 *>(c_l1 + W + c0);
+                        const float4 w1b = *reinterpret_cast<const float4 *>(c_l1 + W + c0 + 4);
+                        const float4 w2a = *reinterpret_cast<const float4 *>(c_l1 + 2 * W + c0);
+                        const float4 w2b = *reinterpret_cast<const float4 *>(c_l1 + 2 * W + c0 + 4);
+                        const float4 ba = *reinterpret_cast<const float4 *>(b1 + c0);
+                        const float4 bb = *reinterpret_cast<const float4 *>(b1 + c0 + 4);
+                        const float4 aa = *reinterpret_cast<const float4 *>(a1 + c0);
+                        const float4 ab4 = *reinterpret_cast<const float4 *>(a1 + c0 + 4);
+                        const float w0v[8] = {w0a.x, w0a.y, w0a.z, w0a.w, w0b.x, w0b.y, w0b.z, w0b.w};
+                        const float w1v[8] = {w1a.x, w1a.y, w1a.z, w1a.w, w1b.x, w1b.y, w1b.z, w1b.w};
+                        const float w2v[8] = {w2a.x, w2a.y, w2a.z, w2a.w, w2b.x, w2b.y, w2b.z, w2b.w};
+                        const float bv[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
+                        const float av[8] = {aa.x, aa.y, aa.z, aa.w, ab4.x, ab4.y, ab4.z, ab4.w};
+                        float h8[8];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        float u = fmaf(w0v[i], x0, bv[i]);
-                        u = fmaf(w1v[i], x1, u);
-                        u = fmaf(w2v[i], x2, u);
-                        const float hv = activate<ACT>(u);
-                        h8[i] = hv;
-                        ta = fmaf(av[i], hv, ta);
+                        for (int i = 0; i < 8; ++i) {
+                            float u = fmaf(w0v[i], x0, bv[i]);
+                            u = fmaf(w1v[i], x1, u);
+                            u = fmaf(w2v[i], x2, u);
+                            const float hv = activate<ACT>(u);
+                            h8[i] = hv;
+                            ta = fmaf(av[i], hv, ta);
+                        }
+                        if (write_first) st_a8(c0, h8);
                     }
-                    if (write_first) st_a8(c0, h8);
+                    if (write_first) signal(&a_ready[kb], true);
                 }
-                if (write_first) signal_a();
                 float sb = 0.f;
                 exchange(ta, sb);
                 if (slice == 0) {
@@ -535,21 +550,23 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                     if (d == 1 && idx >= 0) out[idx] = y;
                 }
             } else {
-                // Fourier features gamma(x) = [sin 2 pi s, cos 2 pi s]; in_dim == W, same unit slices as the layers
-                for (int k0 = u0; k0 < u0 + quarter; k0 += 8) {
-                    float h8[8];
+                // Fourier features gamma(x) = [sin 2 pi s, cos 2 pi s]; in_dim == W, same slices as the layers
+                for (int kb = 0; kb < KB; ++kb) {
+                    for (int k0 = 64 * kb + 16 * slice; k0 < 64 * kb + 16 * slice + 16; k0 += 8) {
+                        float h8[8];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int k = k0 + i;
-                        const int kk = k < P.m ? k : k - P.m;
-                        const float ph = fourier_phase(P.B + 3 * kk, x0, x1, x2);
-                        float sv, cv;
-                        sincospif(2.0f * ph, &sv, &cv);
-                        h8[i] = k < P.m ? sv : cv;
+                        for (int i = 0; i < 8; ++i) {
+                            const int k = k0 + i;
+                            const int kk = k < P.m ? k : k - P.m;
+                            const float ph = fourier_phase(P.B + 3 * kk, x0, x1, x2);
+                            float sv, cv;
+                            sincospif(2.0f * ph, &sv, &cv);
+                            h8[i] = k < P.m ? sv : cv;
+                        }
+                        st_a8(k0, h8);
                     }
-                    st_a8(k0, h8);
+                    signal(&a_ready[kb], true);
                 }
-                signal_a();
             }
             // ---- tensor-core layers
             for (int l = P.first_mma; l <= Dt && ok; ++l) {
@@ -560,15 +577,34 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                 const bool last = l == Dt;
                 const float *cs = c_all + (size_t)(l - 1) * 3 * W;
                 const float c1 = P.c1[l - 1];
-                float sa = 0.f, sb = 0.f;
-                if (quarter >= 32) {
-                    for (int c0 = u0; c0 < u0 + quarter; c0 += 32)
-                        epilogue_chunk<MODE, ACT, TAIL, 32>(cs, W, c1, t_lane, c0, !last, a_hi_l, a_lo_l, sa, sb);
-                } else {
-                    epilogue_chunk<MODE, ACT, TAIL, 16>(cs, W, c1, t_lane, u0, !last, a_hi_l, a_lo_l, sa, sb);
+                // drain the accumulator: K-blocks 0-1 to registers, 2-3 (if any) through shared memory
+                const int et = threadIdx.x - 64;
+                uint32_t v0[16], v1[16];
+                tmem_ld16(t_lane + (uint32_t)(16 * slice), v0);
+                if (KB > 1) tmem_ld16(t_lane + (uint32_t)(64 + 16 * slice), v1);
+                for (int kb = 2; kb < KB; ++kb) {
+                    uint32_t tmp[16];
+                    tmem_ld16(t_lane + (uint32_t)(64 * kb + 16 * slice), tmp);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) dbuf[((kb - 2) * 16 + i) * kEpiThreads + et] = __uint_as_float(tmp[i]);
                 }
-                if (!last) signal_a();
-                else tc_fence_before();
+                tmem_wait_ld();
+                signal(d_drained, false);  // the next layer may overwrite the accumulator
+                float sa = 0.f, sb = 0.f;
+                epilogue16<MODE, ACT, TAIL>(cs, W, c1, v0, 16 * slice, !last, a_hi_l, a_lo_l, sa, sb);
+                if (!last) signal(&a_ready[0], true);
+                if (KB > 1) {
+                    epilogue16<MODE, ACT, TAIL>(cs, W, c1, v1, 64 + 16 * slice, !last, a_hi_l, a_lo_l, sa, sb);
+                    if (!last) signal(&a_ready[1], true);
+                }
+                for (int kb = 2; kb < KB; ++kb) {
+                    uint32_t tmp[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) tmp[i] = __float_as_uint(dbuf[((kb - 2) * 16 + i) * kEpiThreads + et]);
+                    epilogue16<MODE, ACT, TAIL>(cs, W, c1, tmp, 64 * kb + 16 * slice, !last, a_hi_l, a_lo_l, sa, sb);
+                    if (!last) signal(&a_ready[kb], true);
+                }
                 exchange(sa, sb);
                 if (slice == 0) {
                     const float t0v = sa + __ldg(P.tb + 2 * (l - 1));

@@ -48,7 +48,9 @@ struct TcPack {
 
 size_t tc_smem_bytes(const TcParams &P, int parts) {
     (void)parts;  // the A operand lives in TMEM
+    const int kb = P.W / 64;
     return 1024 /*alignment slack*/ + (size_t)P.n_stages * P.stage_bytes +
+           (size_t)(kb > 2 ? kb - 2 : 0) * 16 * kEpiThreads * 4 /*accumulator drain buffer*/ +
            (size_t)4 * (3 * P.W + (size_t)3 * P.L * P.W) /*first-layer weights, per-layer constants*/ + kMiscBytes;
 }
 
