@@ -179,6 +179,114 @@ def run_reference(args):
     return 0
 
 
+def serve_models(sand):
+    """The three resident models of the serving workload, each with its own level-7 octree."""
+    specs = [(synth.siren_tmlp(8, 256, seed=1), synth.scene_octree(7, 8)),
+             (synth.siren_tmlp(8, 336, seed=2), synth.scene_octree(7, 8, transform=synth.rotation([0, 1, 0], 0.5), scale=0.95)),
+             (synth.relu_ff_tmlp(6, 128, n_freq=64, sigma=10.0, seed=3),
+              synth.scene_octree(7, 6, transform=synth.rotation([1, 1, 0], 0.7), scale=0.9))]
+    models = []
+    for model, tree in specs:
+        m = sand.Model.from_params(*model.header_ints(), model.omega0, model.flat(), device=0)
+        m.set_depth_map(tree.max_level, tree.n_layers, tree.child, tree.depth, tree.far)
+        models.append(m)
+    return models
+
+
+def serve_requests(count: int, seed: int):
+    """Request pool: half marching-cubes blocks (side 32/64/128/256 with equal probability, a
+    side^3 lattice over a random sub-cube), half ray-sample batches (n log-uniform in
+    [4096, 2^21], points along random rays through the domain); model uniform over 3."""
+    import torch
+    g = np.random.Generator(np.random.PCG64(seed))
+    pool = []
+    for _ in range(count):
+        if g.random() < 0.5:
+            side = int(g.choice([32, 64, 128, 256]))
+            ext = g.uniform(0.25, 2.0)
+            lo = g.uniform(-1.0, 1.0 - ext, 3)
+            t = np.arange(side, dtype=np.float64) / max(side - 1, 1) * ext
+            z, y, x = np.meshgrid(t + lo[2], t + lo[1], t + lo[0], indexing="ij")
+            pts = np.stack([x.ravel(), y.ravel(), z.ravel()], 1).astype(np.float32)
+        else:
+            n = int(np.exp(g.uniform(np.log(4096), np.log(1 << 21))))
+            o = g.uniform(-1, 1, (n, 3)); d = g.normal(size=(n, 3)); d /= np.linalg.norm(d, axis=1, keepdims=True)
+            pts = np.clip(o + d * g.uniform(0, 0.5, (n, 1)), -1.2, 1.2).astype(np.float32)
+        pool.append((int(g.integers(3)), torch.from_numpy(pts).pin_memory()))
+    return pool
+
+
+def serve_bench(sand, models, precision, pool, run_s: float, mem_budget: int = 16 << 30):
+    """Saturation throughput (closed burst of the pool) and Poisson open-loop runs at 0.5x
+    and 0.8x of it: p50 / p99 request latency and aggregate queries/s."""
+    import threading
+    import torch
+    precs = {"bf16": ["bf16", "bf16", "bf16"], "fp32": ["fp32", "fp32_simt", "fp32"]}[precision]
+    out = {"precision_per_model": precs}
+    srv = sand.Server(models, precision=precs, n_streams=4, mem_budget=mem_budget, max_batch_points=1 << 22)
+    outs = [torch.empty(p.shape[0], dtype=torch.float32).pin_memory() for _, p in pool]
+    for i in range(min(4, len(pool))):  # warm up
+        srv.wait(srv.submit(pool[i][0], pool[i][1], outs[i]))
+    srv.close()
+    srv = sand.Server(models, precision=precs, n_streams=4, mem_budget=mem_budget, max_batch_points=1 << 22)
+    t0 = time.perf_counter()
+    tk = [srv.submit(m, p, outs[i]) for i, (m, p) in enumerate(pool)]
+    for t in tk:
+        srv.wait(t)
+    sat_s = time.perf_counter() - t0
+    pts_total = sum(p.shape[0] for _, p in pool)
+    srv.close()
+    sat_qps = pts_total / sat_s
+    out["saturation_qps"] = sat_qps
+    mean_pts = pts_total / len(pool)
+    g = np.random.Generator(np.random.PCG64(99))
+    for frac in (0.5, 0.8):
+        lam = frac * sat_qps / mean_pts  # requests per second
+        srv = sand.Server(models, precision=precs, n_streams=4, mem_budget=mem_budget, max_batch_points=1 << 22)
+        free = list(range(len(pool)))
+        lock = threading.Lock()
+        pending = []
+        done = threading.Event()
+
+        def waiter():
+            while not (done.is_set() and not pending):
+                with lock:
+                    item = pending.pop(0) if pending else None
+                if item is None:
+                    time.sleep(0.0005)
+                    continue
+                t, i = item
+                srv.wait(t)
+                with lock:
+                    free.append(i)
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        t_end = time.perf_counter() + run_s
+        nxt = time.perf_counter()
+        sent = 0
+        while time.perf_counter() < t_end:
+            nxt += g.exponential(1.0 / lam)
+            while time.perf_counter() < nxt:
+                time.sleep(max(0.0, min(0.002, nxt - time.perf_counter())))
+            with lock:
+                i = free.pop(int(g.integers(len(free)))) if free else None
+            if i is None:
+                continue  # every buffer is in flight: the request is dropped (counted below)
+            t = srv.submit(pool[i][0], pool[i][1], outs[i])
+            with lock:
+                pending.append((t, i))
+            sent += 1
+        done.set()
+        th.join()
+        st = srv.stats()
+        srv.close()
+        out["load_%.1f" % frac] = {"offered_requests_per_s": lam, "requests": st["requests"], "p50_ms": st["p50_ms"],
+                                   "p99_ms": st["p99_ms"], "max_ms": st["max_ms"], "queries_per_s": st["queries_per_s"],
+                                   "batches": st["batches"], "seconds": run_s}
+    return out
+
+
 def run_profile_case(args):
     """The same model and map as the benchmark on a smaller point set, for ncu captures."""
     import torch
@@ -214,6 +322,7 @@ def main():
                     help="small profiling case: only (warmup + steps) SAND queries on a grid^3 lattice, or full-depth "
                          "queries on grid^3 uniform points; prints one line")
     ap.add_argument("--grid", type=int, default=GRID)
+    ap.add_argument("--serve-seconds", type=float, default=6.0, help="length of each open-loop serving run (0 = skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -350,6 +459,15 @@ def main():
                 "traffic": kernel_traffic(prec), "kernel": KERNEL_NAME[prec],
                 "peak_source": "%s bf16 sustained %.1f TFLOP/s x %.3g (%s)" % (pk_src, base, ratio, prec)}
 
+    # ---- serving: continuous batching over three resident models (rank 0 only)
+    serve = None
+    if rank == 0 and args.serve_seconds > 0:
+        smodels = serve_models(sand)
+        pool = serve_requests(40, seed=5)
+        serve = {p: serve_bench(sand, smodels, p, pool, args.serve_seconds) for p in ("bf16", "fp32")}
+        for sm in smodels:
+            sm.free()
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(model, tree, pts)
@@ -383,6 +501,8 @@ def main():
         "gpu_launches": 4 * K,
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "serve": serve,
+        "serve_p99_ms": (serve or {}).get("bf16", {}).get("load_0.8", {}).get("p99_ms"),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -191,6 +191,47 @@ typedef struct {
 } sand_query_stats;
 sand_status sand_read_stats(sand_model m, const void *d_workspace, sand_query_stats *out, void *stream);
 
+/* ---------------------------------------------------------------- serving
+ * Continuous batching over resident models (the paper has no serving layer;
+ * this serves the query of Sec. 3.4 to many concurrent clients).  Requests carry
+ * host buffers (pinned memory lets the copies overlap); a scheduler thread keeps
+ * up to n_streams batches in flight, packing each model's queued requests in
+ * arrival order into one query while the batch fits max_batch_points and the free
+ * part of a device arena of mem_budget bytes reserved at creation (a request
+ * needs 16 + sand_workspace_bytes bytes per point); requests that arrive while
+ * batches run join the next batch as a stream and memory free up.  Every result
+ * is identical to running the request alone through sand_query_sdf.  The models
+ * must stay alive and must not be queried concurrently by the caller while the
+ * server runs. */
+typedef struct sand_server_s *sand_server;
+typedef struct {
+    int32_t n_streams;          /* batches in flight (default 3, at most 16) */
+    int32_t precision;          /* sand_precision of every query */
+    size_t mem_budget;          /* device arena for in-flight batches (default 1 GiB) */
+    int64_t max_batch_points;   /* upper bound of points per batch (default 2^22; a larger request runs alone) */
+    const int32_t *model_precision; /* optional [n_models]: per-model sand_precision overriding `precision` */
+} sand_server_opts;
+typedef struct {
+    int64_t requests, batches, points;   /* completed so far */
+    double p50_ms, p99_ms, max_ms;       /* submit-to-result latency of completed requests */
+    double queries_per_s;                /* points completed / (last completion - first submit) */
+    size_t arena_bytes;
+} sand_server_report;
+/* Start a server over n_models loaded models (all on one device).  Packs their
+ * weights for opts->precision and reserves the arena; nothing is allocated later. */
+sand_status sand_server_create(const sand_model *models, int n_models, const sand_server_opts *opts, sand_server *out);
+/* Queue a request: SDF of h_points[n][3] under model `model` into h_out[n].  Both
+ * buffers must stay valid until sand_server_wait returns for *ticket. */
+sand_status sand_server_submit(sand_server s, int model, const float *h_points, int64_t n, float *h_out,
+                               uint64_t *ticket);
+/* Block until the request completed (SAND_ETIMEOUT after timeout_s seconds);
+ * *latency_ms (nullable) receives its submit-to-result time. */
+sand_status sand_server_wait(sand_server s, uint64_t ticket, double timeout_s, double *latency_ms);
+/* Latency percentiles and throughput of the requests completed so far. */
+sand_status sand_server_stats(sand_server s, sand_server_report *out);
+/* Finish queued work, stop the threads, release streams and the arena. */
+sand_status sand_server_destroy(sand_server s);
+
 /* Describe a loaded model. */
 sand_status sand_model_desc(sand_model m, sand_tmlp_desc *out);
 

@@ -6,7 +6,7 @@ include/sand.h; this package builds libsand.so in-tree and exposes it through
 ctypes with PyTorch tensors for device memory and streams.
 """
 from .binding import (ACT_RELU, ACT_SINE, ENC_FOURIER, ENC_NONE, FLAG_NAN_INPUT, FLAG_TIMEOUT, PRECISION,
-                      TAIL_LINEAR, TAIL_MULT, Model, SandError, SandSDF, lib)
+                      TAIL_LINEAR, TAIL_MULT, Model, SandError, SandSDF, Server, lib)
 
-__all__ = ["Model", "SandSDF", "SandError", "lib", "PRECISION", "TAIL_LINEAR", "TAIL_MULT", "ACT_SINE",
+__all__ = ["Model", "Server", "SandSDF", "SandError", "lib", "PRECISION", "TAIL_LINEAR", "TAIL_MULT", "ACT_SINE",
            "ACT_RELU", "ENC_NONE", "ENC_FOURIER", "FLAG_NAN_INPUT", "FLAG_TIMEOUT"]

@@ -49,6 +49,17 @@ class QueryOpts(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_size_t), ("stage_events", ctypes.c_void_p)]
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("n_streams", ctypes.c_int32), ("precision", ctypes.c_int32), ("mem_budget", ctypes.c_size_t),
+                ("max_batch_points", ctypes.c_int64), ("model_precision", ctypes.c_void_p)]
+
+
+class ServerReport(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_int64), ("batches", ctypes.c_int64), ("points", ctypes.c_int64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("queries_per_s", ctypes.c_double), ("arena_bytes", ctypes.c_size_t)]
+
+
 class QueryStats(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_uint32), ("n_network", ctypes.c_uint32), ("count", ctypes.c_uint32 * 16)]
 
@@ -56,7 +67,8 @@ class QueryStats(ctypes.Structure):
 _lib = None
 EXPORTS = ("sand_load_tmlp", "sand_load_tmlp_mem", "sand_load_depth_map", "sand_load_depth_map_mem",
            "sand_workspace_bytes", "sand_query_sdf", "sand_query_sdf_grad", "sand_query_sdf_host",
-           "sand_read_stats", "sand_model_desc", "sand_free", "sand_last_error")
+           "sand_read_stats", "sand_model_desc", "sand_free", "sand_last_error", "sand_server_create",
+           "sand_server_submit", "sand_server_wait", "sand_server_stats", "sand_server_destroy")
 
 
 def lib() -> ctypes.CDLL:
@@ -82,6 +94,11 @@ def lib() -> ctypes.CDLL:
     L.sand_model_desc.argtypes = [P, ctypes.POINTER(TmlpDesc)]
     L.sand_free.argtypes = [P]
     L.sand_last_error.restype = ctypes.c_char_p
+    L.sand_server_create.argtypes = [P, I32, ctypes.POINTER(ServerOpts), ctypes.POINTER(P)]
+    L.sand_server_submit.argtypes = [P, I32, P, I64, P, ctypes.POINTER(ctypes.c_uint64)]
+    L.sand_server_wait.argtypes = [P, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    L.sand_server_stats.argtypes = [P, ctypes.POINTER(ServerReport)]
+    L.sand_server_destroy.argtypes = [P]
     for name in EXPORTS:
         if name not in ("sand_workspace_bytes", "sand_last_error"):
             getattr(L, name).restype = ctypes.c_int
@@ -281,3 +298,68 @@ class SandSDF(torch.autograd.Function):
     def backward(ctx, grad_out):
         (g,) = ctx.saved_tensors
         return grad_out[:, None] * g, None, None, None
+
+
+class Server:
+    """Continuous-batching server over resident models (sand_server_* in include/sand.h).
+
+    submit() takes host points (numpy float32 [n, 3] or a CPU tensor; pinned memory lets
+    the copies overlap) and returns a ticket; wait() returns (sdf, latency_ms).
+    """
+
+    def __init__(self, models, precision="fp32", n_streams: int = 3, mem_budget: int = 1 << 30,
+                 max_batch_points: int = 1 << 22):
+        """precision: one name for every model, or a list with one name per model."""
+        self.models = list(models)
+        precs = [precision] * len(self.models) if isinstance(precision, str) else list(precision)
+        if len(precs) != len(self.models) or any(p not in PRECISION for p in precs):
+            raise ValueError("precision must be one of %s (or one per model)" % sorted(PRECISION))
+        arr = (ctypes.c_void_p * len(self.models))(*[m._h for m in self.models])
+        per = (ctypes.c_int32 * len(self.models))(*[PRECISION[p] for p in precs])
+        o = ServerOpts(int(n_streams), PRECISION[precs[0]], int(mem_budget), int(max_batch_points),
+                       ctypes.cast(per, ctypes.c_void_p))
+        h = ctypes.c_void_p()
+        _check(lib().sand_server_create(arr, len(self.models), ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self._live = {}
+
+    def submit(self, model: int, points, out=None) -> int:
+        if isinstance(points, torch.Tensor):
+            if points.device.type != "cpu" or points.dtype != torch.float32:
+                raise ValueError("host points must be a float32 CPU tensor")
+            pts = points.contiguous()
+            n = pts.shape[0]
+            out = out if out is not None else torch.empty(n, dtype=torch.float32, pin_memory=pts.is_pinned())
+            pp, op = pts.data_ptr(), out.data_ptr()
+        else:
+            pts = np.ascontiguousarray(points, np.float32).reshape(-1, 3)
+            n = pts.shape[0]
+            out = out if out is not None else np.empty(n, np.float32)
+            pp, op = pts.ctypes.data, out.ctypes.data
+        t = ctypes.c_uint64()
+        _check(lib().sand_server_submit(self._h, int(model), ctypes.c_void_p(pp), n, ctypes.c_void_p(op), ctypes.byref(t)))
+        self._live[t.value] = (pts, out)
+        return t.value
+
+    def wait(self, ticket: int, timeout: float = 120.0):
+        lat = ctypes.c_double()
+        st = lib().sand_server_wait(self._h, ctypes.c_uint64(ticket), float(timeout), ctypes.byref(lat))
+        _, out = self._live.pop(ticket, (None, None))
+        _check(st)
+        return out, lat.value
+
+    def stats(self) -> dict:
+        r = ServerReport()
+        _check(lib().sand_server_stats(self._h, ctypes.byref(r)))
+        return {k: getattr(r, k) for k, _ in ServerReport._fields_}
+
+    def close(self):
+        if self._h:
+            lib().sand_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

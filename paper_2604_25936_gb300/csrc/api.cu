@@ -214,6 +214,16 @@ bool model_precision_ready(sand_model m, int precision) {
     return m->tc.packed_precision == precision && m->tc.d_pack != nullptr;
 }
 
+sand_status model_prepare(sand_model m, int precision) {
+    if (precision == SAND_FP32_SIMT) return SAND_OK;
+    if (!tc_supported(m->desc, precision)) {
+        set_error("precision %d is not supported for this model on the tensor-core path", precision);
+        return SAND_EUNSUPPORTED;
+    }
+    DeviceGuard g(m->device);
+    return tc_prepare(&m->tc, m->desc, m->params.data(), precision);
+}
+
 }  // namespace sand
 
 using namespace sand;

@@ -125,5 +125,6 @@ cudaError_t launch_init_header(void *ws, cudaStream_t s);
 int model_device(sand_model m);
 bool model_has_map(sand_model m);
 bool model_precision_ready(sand_model m, int precision);  // device weights for `precision` exist already
+sand_status model_prepare(sand_model m, int precision);   // pack device weights for `precision` (may allocate)
 
 }  // namespace sand

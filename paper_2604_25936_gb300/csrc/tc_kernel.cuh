@@ -55,7 +55,7 @@ constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 constexpr int kSmemBudget = 227 * 1024;
 constexpr int kMaxStages = 8;
-constexpr int kMaxKBlocks = 4;  // W <= 256
+constexpr int kMaxKBlocks = 6;  // K padded to a multiple of 64, W <= 336
 constexpr int kNumBars = 2 * kMaxStages + kMaxKBlocks + 5;  // full, empty, a_ready[kb], d_full, d_drained, drain, x_full, x_empty
 // bytes after the weight stages and constants: barriers, TMEM slot + abort flag,
 // tail exchange (3 slices x 2 values x 128 rows)
@@ -68,6 +68,8 @@ struct TcParams {
     int n_stages;
     uint32_t stage_bytes;     // W * 128
     uint32_t tmem_cols;       // power of two >= W + parts * W / 2
+    int box_rows;             // rows per TMA box: W, or W / 2 when W > 256 (box dimensions are at most 256)
+    int n_split;              // first MMA column group when W > 256 (a multiple of 16)
     float c1[kMaxLayers];     // per layer: w0 / (2 pi s) (sine) or 1 / s (ReLU)
     const float *cvec;        // [L][3][W]: bias' (w0 b / 2 pi for sine, b for ReLU), tail a, tail b
     const float *w1p;         // [3][W] first-layer weights (times w0 / 2 pi for sine), transposed
@@ -299,10 +301,12 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int W = P.W, L = P.L;
-    const int KB = W >> 6;  // K-blocks of 64 units
+    const int KB = (W + 63) >> 6;   // K-blocks of 64 units (the last one partial when W % 64 != 0)
+    const int KS = W >> 4;          // K-steps of 16 holding real units
+    const bool drain_first = (W & 63) == 0 && KB <= 4;  // else: serial epilogue (see below)
     uint8_t *stage_base = smem;
     float *dbuf = reinterpret_cast<float *>(stage_base + (size_t)P.n_stages * P.stage_bytes);  // [(KB-2)*16][512]
-    float *c_l1 = dbuf + (size_t)(KB > 2 ? KB - 2 : 0) * 16 * kEpiThreads;                     // [3][W] first-layer weights
+    float *c_l1 = dbuf + (size_t)(drain_first && KB > 2 ? KB - 2 : 0) * 16 * kEpiThreads;      // [3][W] first-layer weights
     float *c_all = c_l1 + 3 * W;                                                                // [L][3][W]
     uint64_t *bars = reinterpret_cast<uint64_t *>(c_all + (size_t)3 * L * W);
     uint64_t *full_bar = bars;
@@ -361,15 +365,17 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
                 const int Dt = tile_depth(t);
                 for (int l = P.first_mma; l <= Dt && ok; ++l) {
-                    const int kb_n = (l == 1 ? P.D : W) >> 6;
+                    const int kb_n = ((l == 1 ? P.D : W) + 63) >> 6;
                     for (int kb = 0; kb < kb_n && ok; ++kb)
                         for (int p = 0; p < PARTS && ok; ++p, ++it) {
                             const uint32_t s = it % P.n_stages, ph = (it / P.n_stages) & 1;
                             ok = mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1, abort, hdr, 1, true);
                             if (!ok) break;
                             mbar_arrive_tx(smem_u32(&full_bar[s]), P.stage_bytes);
-                            tma_load_2d(smem_u32(stage_base + (size_t)s * P.stage_bytes), &wmap, smem_u32(&full_bar[s]),
-                                        kb * 64, ((l - P.first_mma) * PARTS + p) * W);
+                            const int row0 = ((l - P.first_mma) * PARTS + p) * W;
+                            for (int bx = 0; bx < W; bx += P.box_rows)  // one box of W rows, or two of W/2
+                                tma_load_2d(smem_u32(stage_base + (size_t)s * P.stage_bytes + (size_t)bx * 128), &wmap,
+                                            smem_u32(&full_bar[s]), kb * 64, row0 + bx);
                         }
                 }
             }
@@ -387,10 +393,12 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t ab = MODE == TC_BF16 ? 1u : 0u;
-            const uint32_t idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(W >> 3) << 17) |
-                                   ((uint32_t)(kTileM >> 4) << 24);
+            const int n0 = W <= 256 ? W : P.n_split, n1 = W - n0;  // MMA N <= 256: two column groups when W > 256
+            const uint32_t id_base = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(kTileM >> 4) << 24);
+            const uint32_t idesc0 = id_base | ((uint32_t)(n0 >> 3) << 17);
+            const uint32_t idesc1 = id_base | ((uint32_t)(n1 >> 3) << 17);
             uint32_t it = 0, pdr = 0;
-            uint32_t pa[kMaxKBlocks] = {0, 0, 0, 0};
+            uint32_t pa[kMaxKBlocks] = {0, 0, 0, 0, 0, 0};
             bool ok = true, any_layer = false;
             for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
                 const int Dt = tile_depth(t);
@@ -401,7 +409,8 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                         if (!ok) break;
                     }
                     any_layer = true;
-                    const int kb_n = (l == 1 ? P.D : W) >> 6;
+                    const int kb_n = ((l == 1 ? P.D : W) + 63) >> 6;
+                    const int ks_n = (l == 1 ? P.D : W) >> 4;
                     for (int kb = 0; kb < kb_n && ok; ++kb) {
                         ok = mbar_wait(smem_u32(&a_ready[kb]), pa[kb], abort, hdr, 2, true);
                         pa[kb] ^= 1;
@@ -416,13 +425,23 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
 #pragma unroll
                             for (int ks = 0; ks < 4; ++ks) {
                                 const int g = kb * 4 + ks;
+                                if (g >= ks_n) break;  // zero padding of the last K-block
                                 const uint64_t bd = smem_desc(b_addr + ks * 32);
                                 const uint32_t acol = (uint32_t)g * 8u;  // 16 fp16 K-elements = 8 TMEM columns
                                 if (p == 0) {
-                                    mma_ts(tmem, a_hi + acol, bd, idesc, g != 0);
-                                    if (PARTS == 2) mma_ts(tmem, a_lo + acol, bd, idesc, 1);
+                                    mma_ts(tmem, a_hi + acol, bd, idesc0, g != 0);
+                                    if (PARTS == 2) mma_ts(tmem, a_lo + acol, bd, idesc0, 1);
                                 } else {
-                                    mma_ts(tmem, a_hi + acol, bd, idesc, 1);
+                                    mma_ts(tmem, a_hi + acol, bd, idesc0, 1);
+                                }
+                                if (n1 > 0) {  // units n0 .. W-1: B rows from n0 on, accumulator columns from n0 on
+                                    const uint64_t bd1 = smem_desc(b_addr + (uint32_t)n0 * 128u + ks * 32);
+                                    if (p == 0) {
+                                        mma_ts(tmem + (uint32_t)n0, a_hi + acol, bd1, idesc1, g != 0);
+                                        if (PARTS == 2) mma_ts(tmem + (uint32_t)n0, a_lo + acol, bd1, idesc1, 1);
+                                    } else {
+                                        mma_ts(tmem + (uint32_t)n0, a_hi + acol, bd1, idesc1, 1);
+                                    }
                                 }
                             }
                             mma_commit(smem_u32(&empty_bar[s]));
@@ -513,7 +532,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                 const float *b1 = c_all;       // bias' of layer 1
                 const float *a1 = c_all + W;   // tail a of layer 1
                 for (int kb = 0; kb < KB; ++kb) {
-                    for (int c0 = 64 * kb + 16 * slice; c0 < 64 * kb + 16 * slice + 16; c0 += 8) {
+                    for (int c0 = 64 * kb + 16 * slice; c0 < 64 * kb + 16 * slice + 16 && c0 < W; c0 += 8) {
                         const float4 w0a = *reinterpret_cast<const float4 *>(c_l1 + c0);
                         const float4 w0b = *reinterpret_cast<const float4 *>(c_l1 + c0 + 4);
                         const float4 w1a = *reinterpret_cast<const float4 *>(c_l1 + W + c0);
@@ -552,7 +571,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             } else {
                 // Fourier features gamma(x) = [sin 2 pi s, cos 2 pi s]; in_dim == W, same slices as the layers
                 for (int kb = 0; kb < KB; ++kb) {
-                    for (int k0 = 64 * kb + 16 * slice; k0 < 64 * kb + 16 * slice + 16; k0 += 8) {
+                    for (int k0 = 64 * kb + 16 * slice; k0 < 64 * kb + 16 * slice + 16 && k0 < W; k0 += 8) {
                         float h8[8];
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
@@ -577,6 +596,22 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                 const bool last = l == Dt;
                 const float *cs = c_all + (size_t)(l - 1) * 3 * W;
                 const float c1 = P.c1[l - 1];
+                float sa = 0.f, sb = 0.f;
+                if (!drain_first) {
+                    // serial: each K-block read, computed and stored in turn; the next layer may start
+                    // overwriting the accumulator only once every warp has read all of it
+                    for (int kb = 0; kb < KB; ++kb) {
+                        const int c0 = 64 * kb + 16 * slice;
+                        if (c0 < W) {
+                            uint32_t v[16];
+                            tmem_ld16(t_lane + (uint32_t)c0, v);
+                            tmem_wait_ld();
+                            epilogue16<MODE, ACT, TAIL>(cs, W, c1, v, c0, !last, a_hi_l, a_lo_l, sa, sb);
+                        }
+                        if (!last) signal(&a_ready[kb], true);
+                    }
+                    signal(d_drained, false);
+                } else {
                 // drain the accumulator: K-blocks 0-1 to registers, 2-3 (if any) through shared memory
                 const int et = threadIdx.x - 64;
                 uint32_t v0[16], v1[16];
@@ -591,7 +626,6 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                 }
                 tmem_wait_ld();
                 signal(d_drained, false);  // the next layer may overwrite the accumulator
-                float sa = 0.f, sb = 0.f;
                 epilogue16<MODE, ACT, TAIL>(cs, W, c1, v0, 16 * slice, !last, a_hi_l, a_lo_l, sa, sb);
                 if (!last) signal(&a_ready[0], true);
                 if (KB > 1) {
@@ -604,6 +638,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                     for (int i = 0; i < 16; ++i) tmp[i] = __float_as_uint(dbuf[((kb - 2) * 16 + i) * kEpiThreads + et]);
                     epilogue16<MODE, ACT, TAIL>(cs, W, c1, tmp, 64 * kb + 16 * slice, !last, a_hi_l, a_lo_l, sa, sb);
                     if (!last) signal(&a_ready[kb], true);
+                }
                 }
                 exchange(sa, sb);
                 if (slice == 0) {

@@ -23,7 +23,9 @@ static int mode_of(int precision) {
 
 bool tc_supported(const sand_tmlp_desc &d, int precision) {
     if (mode_of(precision) < 0) return false;
-    if (d.width != 64 && d.width != 128 && d.width != 256) return false;
+    if (d.width != 64 && d.width != 128 && d.width != 256 && d.width != 336) return false;
+    // width 336: the accumulator (336 columns) plus one fp16 operand (168) fill TMEM; no room for the float32 split
+    if (d.width == 336 && mode_of(precision) == TC_SPLIT16) return false;
     if (d.encoder == SAND_ENC_FOURIER && d.in_dim != d.width) return false;
     return d.n_layers >= 1;
 }
@@ -48,9 +50,10 @@ struct TcPack {
 
 size_t tc_smem_bytes(const TcParams &P, int parts) {
     (void)parts;  // the A operand lives in TMEM
-    const int kb = P.W / 64;
+    const int kb = (P.W + 63) / 64;
+    const bool drain_first = (P.W % 64) == 0 && kb <= 4;
     return 1024 /*alignment slack*/ + (size_t)P.n_stages * P.stage_bytes +
-           (size_t)(kb > 2 ? kb - 2 : 0) * 16 * kEpiThreads * 4 /*accumulator drain buffer*/ +
+           (size_t)(drain_first && kb > 2 ? kb - 2 : 0) * 16 * kEpiThreads * 4 /*accumulator drain buffer*/ +
            (size_t)4 * (3 * P.W + (size_t)3 * P.L * P.W) /*first-layer weights, per-layer constants*/ + kMiscBytes;
 }
 
@@ -66,7 +69,7 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
     const bool sine = d.activation == SAND_ACT_SINE;
     const int first = d.encoder == SAND_ENC_FOURIER ? 1 : 2;
     const int parts = mode == TC_SPLIT16 ? 2 : 1;
-    const int kpad = W;
+    const int kpad = (W + 63) / 64 * 64;  // K padded with zero weights to whole K-blocks
     const int n_mma = L - first + 1;
     const float *p = params;
     const float *B = nullptr;
@@ -166,7 +169,8 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
     }
     cuuint64_t gdim[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
     cuuint64_t gstride[1] = {(cuuint64_t)kpad * 2};
-    cuuint32_t box[2] = {64, (cuuint32_t)W};
+    const int box_rows = W <= 256 ? W : W / 2;
+    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
     cuuint32_t estride[2] = {1, 1};
     CUresult cr = enc(&pk->map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, dbuf, gdim, gstride, box, estride,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -182,6 +186,8 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
     P.first_mma = first;
     P.kpad = kpad;
     P.stage_bytes = (uint32_t)W * 128u;
+    P.box_rows = box_rows;
+    P.n_split = W <= 256 ? W : 176;
     {   // accumulator (W columns) + A_hi (W/2) [+ A_lo (W/2)], rounded up to a power of two
         uint32_t need = (uint32_t)W + (uint32_t)parts * (uint32_t)(W / 2), cols = 32;
         while (cols < need) cols <<= 1;

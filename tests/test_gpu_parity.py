@@ -291,3 +291,25 @@ def test_full_size_lattice_sampled(scene, prec):
     idx = synth.sample_indices(len(pts), 20000, seed=11)
     y_ref = oracle.query(model, tree, pts[idx])
     check(y.cpu().numpy()[idx].astype(np.float64), y_ref, TOL[prec], "256^3 sampled/" + prec)
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16", "fp32_simt"])
+def test_width_336(prec):
+    """8 x 336 SIREN (the wide variant): two MMA column groups and a zero-padded last K-block
+    on the tensor cores (fp16 / bf16); the float32 split does not fit TMEM at this width."""
+    Model, SandError = _lib()
+    model = synth.siren_tmlp(8, 336, seed=2)
+    tree = synth.scene_octree(7, 8, transform=synth.rotation([0, 1, 0], 0.5), scale=0.95)
+    m = load(model, tree)
+    pts = synth.lattice(48)
+    y_ref, d_ref = oracle.query(model, tree, pts, exit_layers=True)
+    y, el = m.query(dev(pts), precision=prec, exit_layers=True)
+    np.testing.assert_array_equal(el.cpu().numpy().astype(np.int32), d_ref)
+    check(y, y_ref, TOL[prec], "w336/" + prec)
+    full = synth.uniform_points(3001, seed=19)
+    check(m.query(dev(full), precision=prec, full_depth=True), oracle.full_depth(model, full), TOL[prec],
+          "w336 full/" + prec)
+    if prec == "fp16":
+        with pytest.raises(SandError, match="EUNSUPPORTED"):
+            m.query(dev(full), precision="fp32")
+    m.free()
