@@ -103,6 +103,7 @@ struct Batch {
     int64_t points = 0;
     size_t off = 0, bytes = 0;
     cudaEvent_t done = nullptr;
+    bool launched = false;  // set (under the server mutex) once every copy, the query and the event are enqueued
 };
 
 }  // namespace sand
@@ -220,11 +221,12 @@ static void scheduler_loop(sand_server_s *S) {
             S->cv_work.wait(lk);
             continue;
         }
-        S->in_flight[slot] = b;
+        S->in_flight[slot] = b;  // occupies the stream; polled only once launched (an unrecorded event reads as complete)
         cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
         lk.unlock();
         launch_batch(S, slot, b);
         lk.lock();
+        b->launched = true;
         S->cv_work.notify_all();  // wake the completion poller
     }
 }
@@ -236,8 +238,9 @@ static void completion_loop(sand_server_s *S) {
         bool busy = false;
         for (size_t i = 0; i < S->in_flight.size(); ++i) {
             Batch *b = S->in_flight[i];
-            if (!b || !b->done) continue;
+            if (!b) continue;
             busy = true;
+            if (!b->launched) continue;
             const cudaError_t e = cudaEventQuery(b->done);
             if (e == cudaErrorNotReady) continue;
             const auto now = Clock::now();
