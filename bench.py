@@ -38,9 +38,9 @@ N_LAYERS, WIDTH, SEED = 8, 256, 1
 TOL = {"fp32": 1e-5, "fp32_simt": 1e-5, "fp16": 2e-3, "bf16": 2e-3, "fp8": None}
 DTYPE = {"fp32": "f32 (3 x f16 split, f32 accumulate)", "fp32_simt": "f32", "fp16": "f16 (f32 accumulate)",
          "bf16": "bf16 (f32 accumulate)", "fp8": "e4m3 (f32 accumulate)"}
-KERNEL_SRC = {"fp32_simt": "paper_2604_25936_gb300/csrc/tmlp_simt.cu", "fp32": "paper_2604_25936_gb300/csrc/tmlp_tc.cu",
-              "fp16": "paper_2604_25936_gb300/csrc/tmlp_tc.cu", "bf16": "paper_2604_25936_gb300/csrc/tmlp_tc.cu",
-              "fp8": "paper_2604_25936_gb300/csrc/tmlp_tc.cu"}
+KERNEL_SRC = {"fp32_simt": "paper_2604_25936_gb300/csrc/tmlp_simt.cu", "fp32": "paper_2604_25936_gb300/csrc/tc_kernel.cuh",
+              "fp16": "paper_2604_25936_gb300/csrc/tc_kernel.cuh", "bf16": "paper_2604_25936_gb300/csrc/tc_kernel.cuh",
+              "fp8": "paper_2604_25936_gb300/csrc/tc_kernel.cuh"}
 KERNEL_NAME = {"fp32_simt": "tmlp_simt_kernel", "fp32": "tmlp_tc_kernel", "fp16": "tmlp_tc_kernel",
                "bf16": "tmlp_tc_kernel", "fp8": "tmlp_tc_kernel"}
 METRIC = "SDF queries/s, SAND vs full-depth T-MLP on 1 GB300 at stated error; serve p99 ms"
