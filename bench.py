@@ -303,6 +303,104 @@ def serve_bench(sand, models, precision, pool, run_s: float, mem_budget: int = 1
     return out
 
 
+def precision_variant(sand, local: int, steps: int, grid: int = 512, n_err: int = 1 << 20):
+    """8 x 256 and 8 x 336 SAND-SIRENs on a grid^3 lattice with bf16 and FP8 hidden products:
+    SAND and full-depth queries/s, tensor-core TFLOP/s, and the error against the FP64 oracle
+    on n_err uniform points in [-1, 1]^3 (PCG64 seed 7; full depth on the first 20,000)."""
+    import torch
+    import oracle
+    pts = synth.lattice(grid)
+    n = len(pts)
+    x = torch.from_numpy(pts).cuda()
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    upts = synth.uniform_points(n_err, seed=7)
+    ux = torch.from_numpy(upts).cuda()
+    stream = torch.cuda.current_stream()
+    res = {"lattice": "%d^3 (%d points)" % (grid, n), "error_sample": "%d uniform points, PCG64 seed 7" % n_err}
+    for width, seed, tree in ((256, 1, synth.scene_octree(7, 8)),
+                              (336, 2, synth.scene_octree(7, 8, transform=synth.rotation([0, 1, 0], 0.5), scale=0.95))):
+        model = synth.siren_tmlp(8, width, seed=seed)
+        m = sand.Model.from_params(*model.header_ints(), model.omega0, model.flat(), device=local)
+        m.set_depth_map(tree.max_level, tree.n_layers, tree.child, tree.depth, tree.far)
+        ws = m.workspace(n)
+        fws = m.workspace(0)
+        y_ref = oracle.query(model, tree, upts)
+        yf_ref = oracle.full_depth(model, upts[:20000])
+        entry = {}
+        for prec in ("bf16", "fp8"):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            for _ in range(2):
+                m.query(x, precision=prec, out=out, workspace=ws)
+            torch.cuda.synchronize()
+            counts = np.array(m.stats(ws)["count"][:9], np.int64)
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            mlp = []
+            t0.record(stream)
+            for _ in range(steps):
+                m.query(x, precision=prec, out=out, workspace=ws, events=ev)
+            t1.record(stream)
+            torch.cuda.synchronize()
+            sand_ms = t0.elapsed_time(t1) / steps
+            mlp_ms = ev[1].elapsed_time(ev[2])
+            m.query(x, precision=prec, full_depth=True, out=out, workspace=fws)
+            torch.cuda.synchronize()
+            t0.record(stream)
+            for _ in range(2):
+                m.query(x, precision=prec, full_depth=True, out=out, workspace=fws)
+            t1.record(stream)
+            torch.cuda.synchronize()
+            full_ms = t0.elapsed_time(t1) / 2
+            flops = float((flops_per_point(np.arange(9), width, False) * counts).sum())
+            full_flops = float(flops_per_point(np.array([8]), width, False)[0]) * n
+            uy = m.query(ux, precision=prec).double().cpu().numpy()
+            e = np.abs(uy - y_ref)
+            ufy = m.query(ux[:20000], precision=prec, full_depth=True).double().cpu().numpy()
+            entry[prec] = {"sand_queries_per_s": n / (sand_ms / 1e3), "full_depth_queries_per_s": n / (full_ms / 1e3),
+                           "sand_ms": sand_ms, "full_ms": full_ms,
+                           "tmlp_tflops_sand": flops / (mlp_ms / 1e3) / 1e12,
+                           "tflops_full_depth": full_flops / (full_ms / 1e3) / 1e12,
+                           "max_abs_err": float(e.max()), "rms_err": float(np.sqrt((e ** 2).mean())),
+                           "max_abs_err_full_depth_20k": float(np.abs(ufy - yf_ref).max())}
+        res["8x%d" % width] = entry
+        m.free()
+    return res
+
+
+def trace_bench(sand, model, tree, local: int, steps: int, precision: str = "fp32"):
+    """Sphere tracing of a 1920 x 1080 pinhole image (vertical FOV 45 degrees, eye on a radius-2.5
+    orbit at azimuth 30, elevation 20, looking at the origin), at most 64 SAND queries per ray,
+    hit at |y| < 1e-4, then the input gradient (normal) at the hits."""
+    import torch
+    eye, dirs = synth.pinhole_rays(1920, 1080, fov_y_deg=45.0, radius=2.5, azimuth_deg=30.0, elevation_deg=20.0)
+    e, d = torch.from_numpy(eye).cuda(), torch.from_numpy(dirs).cuda()
+    m = sand.Model.from_params(*model.header_ints(), model.omega0, model.flat(), device=local)
+    m.set_depth_map(tree.max_level, tree.n_layers, tree.child, tree.depth, tree.far)
+    stream = torch.cuda.current_stream()
+    res = {"rays": len(dirs), "max_steps": 64, "hit_eps": 1e-4, "precision": precision,
+           "normals": "gradient on the CUDA cores (float32)"}
+    for normals in (False, True):
+        for _ in range(2):
+            out = m.sphere_trace(e, d, max_steps=64, hit_eps=1e-4, precision=precision, normals=normals)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps):
+            out = m.sphere_trace(e, d, max_steps=64, hit_eps=1e-4, precision=precision, normals=normals)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / steps
+        res["ms_with_normals" if normals else "ms"] = ms
+    _, st, ks, _ = out
+    st, ks = st.cpu().numpy(), ks.cpu().numpy()
+    q = int(ks.astype(np.int64).sum())
+    res.update({"sdf_queries": q, "queries_per_s": q / (res["ms"] / 1e3), "rays_per_s": len(dirs) / (res["ms"] / 1e3),
+                "hits": int((st == 1).sum()), "missed": int((st == 0).sum()), "step_limit": int((st == 2).sum()),
+                "normal_pass_ms": res["ms_with_normals"] - res["ms"],
+                "steps_histogram_16": np.bincount(np.minimum(ks, 64) // 4, minlength=17).tolist()})
+    m.free()
+    return res
+
+
 def run_profile_case(args):
     """The same model and map as the benchmark on a smaller point set, for ncu captures."""
     import torch
@@ -334,6 +432,8 @@ def main():
     ap.add_argument("--impl", default="sand", choices=["sand", "reference"])
     ap.add_argument("--precision", default="fp32", choices=sorted(TOL))
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the 512^3 bf16 / FP8 precision variant and the sphere-tracing workload")
     ap.add_argument("--profile", choices=["sand", "full"], default=None,
                     help="small profiling case: only (warmup + steps) SAND queries on a grid^3 lattice, or full-depth "
                          "queries on grid^3 uniform points; prints one line")
@@ -477,6 +577,14 @@ def main():
         for sm in smodels:
             sm.free()
 
+    tr = None
+    if rank == 0 and not args.no_variants:
+        tr = trace_bench(sand, model, synth.scene_octree(7, N_LAYERS, far_field=True), local, max(3, K // 4))
+
+    variant = None
+    if rank == 0 and not args.no_variants:
+        variant = precision_variant(sand, local, max(3, K // 4))
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(model, tree, pts)
@@ -511,6 +619,8 @@ def main():
         "clocks": clocks,
         "cpu_baseline": cpu,
         "serve": serve,
+        "precision_variant": variant,
+        "sphere_trace": tr,
         "serve_p99_ms": (serve or {}).get("bf16", {}).get("load_0.8", {}).get("p99_ms"),
     }
     if rank == 0:

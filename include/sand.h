@@ -180,6 +180,39 @@ sand_status sand_query_sdf_host(sand_model m, const float *h_points, int64_t n, 
 sand_status sand_query_sdf_noalloc(sand_model m, const float *d_points, int64_t n, float *d_out,
                                    const sand_query_opts *opts, void *stream);
 
+/* ---------------------------------------------------------------- sphere tracing
+ * Rendering use of the SAND SDF (Sec. 3.4 queries at ray samples; the paper
+ * gives no tracing algorithm, this is classic sphere tracing).  Ray r has origin
+ * o (d_origin[0..2] shared by every ray, or d_origin[3r..3r+2] when
+ * per_ray_origin) and direction d_dirs[3r..3r+2] (float32, not normalised by the
+ * library; unit length makes t a distance).  It starts at t = the parameter where
+ * it enters [-1, 1]^3 (0 when o is inside) and repeats, at most max_steps times:
+ * y = SAND query of p = fma(t, d, o) (float32 per component); |y| < hit_eps gives
+ * SAND_RAY_HIT (t kept); otherwise t <- t + y, and leaving the ray's interval in
+ * the domain gives SAND_RAY_MISS.  A NaN y gives SAND_RAY_NAN, the step limit
+ * SAND_RAY_STEPS.  Rays that never enter the domain are SAND_RAY_MISS with 0 steps.
+ * Outputs (device, caller-owned, each nullable): d_t [n] final t, d_state [n],
+ * d_steps [n] queries made for the ray, d_grad [n][3] the input gradient of
+ * y at the hit points (the surface normal direction, not normalised; 0 for rays
+ * that did not hit), evaluated on the CUDA cores in float32.
+ * qopts: precision and max_depth apply to every step; its other fields must be
+ * zero (the tracer owns its workspace: a grow-only device buffer of
+ * sand_trace_state_bytes(n_rays) kept by the model, so trace calls on one model
+ * must be stream-ordered).  The march is stream-ordered and needs no host round
+ * trip; with poll_every = k > 0 the host reads the active-ray count every k
+ * steps (a stream synchronisation) and stops early when it is 0. */
+typedef enum { SAND_RAY_MISS = 0, SAND_RAY_HIT = 1, SAND_RAY_STEPS = 2, SAND_RAY_NAN = 3 } sand_ray_state;
+typedef struct {
+    int max_steps;     /* 1 .. 255 */
+    float hit_eps;     /* > 0 */
+    int poll_every;    /* 0 = launch all max_steps steps without reading back */
+    int reserved;
+} sand_trace_opts;
+size_t sand_trace_state_bytes(int64_t n_rays);
+sand_status sand_sphere_trace(sand_model m, const float *d_origin, int per_ray_origin, const float *d_dirs,
+                              int64_t n_rays, const sand_trace_opts *topts, const sand_query_opts *qopts, float *d_t,
+                              uint8_t *d_state, uint8_t *d_steps, float *d_grad, void *stream);
+
 /* Flags and counters a query leaves in its workspace (read after the query's
  * stream has been synchronised by this call). */
 #define SAND_FLAG_NAN_INPUT 1u

@@ -6,7 +6,9 @@ include/sand.h; this package builds libsand.so in-tree and exposes it through
 ctypes with PyTorch tensors for device memory and streams.
 """
 from .binding import (ACT_RELU, ACT_SINE, ENC_FOURIER, ENC_NONE, FLAG_NAN_INPUT, FLAG_TIMEOUT, PRECISION,
-                      TAIL_LINEAR, TAIL_MULT, Model, SandError, SandSDF, Server, lib)
+                      RAY_HIT, RAY_MISS, RAY_NAN, RAY_STEPS, TAIL_LINEAR, TAIL_MULT, Model, SandError, SandSDF,
+                      Server, lib)
 
 __all__ = ["Model", "Server", "SandSDF", "SandError", "lib", "PRECISION", "TAIL_LINEAR", "TAIL_MULT", "ACT_SINE",
-           "ACT_RELU", "ENC_NONE", "ENC_FOURIER", "FLAG_NAN_INPUT", "FLAG_TIMEOUT"]
+           "ACT_RELU", "ENC_NONE", "ENC_FOURIER", "FLAG_NAN_INPUT", "FLAG_TIMEOUT", "RAY_MISS", "RAY_HIT", "RAY_STEPS",
+           "RAY_NAN"]

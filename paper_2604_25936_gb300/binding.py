@@ -60,6 +60,14 @@ class ServerReport(ctypes.Structure):
                 ("queries_per_s", ctypes.c_double), ("arena_bytes", ctypes.c_size_t)]
 
 
+class TraceOpts(ctypes.Structure):
+    _fields_ = [("max_steps", ctypes.c_int32), ("hit_eps", ctypes.c_float), ("poll_every", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+RAY_MISS, RAY_HIT, RAY_STEPS, RAY_NAN = 0, 1, 2, 3
+
+
 class QueryStats(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_uint32), ("n_network", ctypes.c_uint32), ("count", ctypes.c_uint32 * 16)]
 
@@ -68,7 +76,8 @@ _lib = None
 EXPORTS = ("sand_load_tmlp", "sand_load_tmlp_mem", "sand_load_depth_map", "sand_load_depth_map_mem",
            "sand_workspace_bytes", "sand_query_sdf", "sand_query_sdf_grad", "sand_query_sdf_host",
            "sand_read_stats", "sand_model_desc", "sand_free", "sand_last_error", "sand_server_create",
-           "sand_server_submit", "sand_server_wait", "sand_server_stats", "sand_server_destroy")
+           "sand_server_submit", "sand_server_wait", "sand_server_stats", "sand_server_destroy",
+           "sand_trace_state_bytes", "sand_sphere_trace")
 
 
 def lib() -> ctypes.CDLL:
@@ -99,8 +108,12 @@ def lib() -> ctypes.CDLL:
     L.sand_server_wait.argtypes = [P, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
     L.sand_server_stats.argtypes = [P, ctypes.POINTER(ServerReport)]
     L.sand_server_destroy.argtypes = [P]
+    L.sand_trace_state_bytes.argtypes = [I64]
+    L.sand_trace_state_bytes.restype = ctypes.c_size_t
+    L.sand_sphere_trace.argtypes = [P, P, I32, P, I64, ctypes.POINTER(TraceOpts), ctypes.POINTER(QueryOpts), P, P, P,
+                                    P, P]
     for name in EXPORTS:
-        if name not in ("sand_workspace_bytes", "sand_last_error"):
+        if name not in ("sand_workspace_bytes", "sand_last_error", "sand_trace_state_bytes"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -253,6 +266,30 @@ class Model:
         _check(lib().sand_query_sdf_host(self._h, ctypes.c_void_p(pp), n, ctypes.c_void_p(op), ctypes.byref(o),
                                          _stream_handle(stream)))
         return out
+
+    def sphere_trace(self, origin: torch.Tensor, dirs: torch.Tensor, max_steps: int = 64, hit_eps: float = 1e-4,
+                     precision: str = "fp32", max_depth: int = 0, normals: bool = True, poll_every: int = 8,
+                     stream: Optional[torch.cuda.Stream] = None):
+        """Sphere-trace rays through the SAND SDF.  origin: [3] (shared) or [n, 3]; dirs: [n, 3].
+        Returns (t [n], state [n] uint8 RAY_*, steps [n] uint8, grad [n, 3] at hits or None)."""
+        d = _as_points(dirs, self.device)
+        n = d.shape[0]
+        o = origin.to(device=d.device, dtype=torch.float32).contiguous()
+        per_ray = o.dim() == 2
+        if (per_ray and tuple(o.shape) != (n, 3)) or (not per_ray and o.numel() != 3):
+            raise ValueError("origin must be [3] or [n, 3]")
+        t = torch.empty(n, dtype=torch.float32, device=d.device)
+        state = torch.empty(n, dtype=torch.uint8, device=d.device)
+        steps = torch.empty(n, dtype=torch.uint8, device=d.device)
+        g = torch.empty((n, 3), dtype=torch.float32, device=d.device) if normals else None
+        to = TraceOpts(int(max_steps), float(hit_eps), int(poll_every), 0)
+        q = self._opts(precision, max_depth, False, None, None)
+        _check(lib().sand_sphere_trace(self._h, ctypes.c_void_p(o.data_ptr()), int(per_ray),
+                                       ctypes.c_void_p(d.data_ptr()), n, ctypes.byref(to), ctypes.byref(q),
+                                       ctypes.c_void_p(t.data_ptr()), ctypes.c_void_p(state.data_ptr()),
+                                       ctypes.c_void_p(steps.data_ptr()),
+                                       ctypes.c_void_p(g.data_ptr() if g is not None else 0), _stream_handle(stream)))
+        return t, state, steps, g
 
     def stats(self, workspace: Optional[torch.Tensor] = None, stream: Optional[torch.cuda.Stream] = None) -> dict:
         """Flags and per-exit-layer counts left by the last query on `workspace` (synchronises the stream)."""

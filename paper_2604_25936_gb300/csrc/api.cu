@@ -25,6 +25,8 @@ struct sand_model_s {
     size_t ws_bytes = 0;
     float *d_stage = nullptr;         // staging for host-memory queries: points then outputs
     size_t stage_bytes = 0;
+    void *d_trace = nullptr;          // sphere-tracer state (rays, active lists, points, workspace)
+    size_t trace_bytes = 0;
 };
 
 namespace sand {
@@ -57,11 +59,6 @@ struct DeviceGuard {
     }
 };
 
-#define SAND_CUDA(call, what)                              \
-    do {                                                   \
-        cudaError_t e_ = (call);                           \
-        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
-    } while (0)
 
 static size_t param_count(const sand_tmlp_desc &d) {
     size_t L = d.n_layers, W = d.width, D = d.in_dim, m = d.n_freq;
@@ -141,6 +138,7 @@ static void release(sand_model_s *m) {
     cudaFree(m->d_far);
     cudaFree(m->d_ws);
     cudaFree(m->d_stage);
+    cudaFree(m->d_trace);
 }
 
 static sand_status ensure_workspace(sand_model_s *m, int64_t n, bool grad, void **ws, size_t *bytes) {
@@ -351,7 +349,7 @@ size_t sand_workspace_bytes(sand_model m, int64_t n, int with_grad) {
 }
 
 static sand_status run_query(sand_model m, const float *d_points, int64_t n, float *d_out, float *d_grad,
-                             const sand_query_opts *opts, void *stream) {
+                             const sand_query_opts *opts, void *stream, const uint32_t *d_count = nullptr) {
     sand_status st = model_precheck(m);
     if (st) return st;
     sand_query_opts o{};
@@ -364,6 +362,7 @@ static sand_status run_query(sand_model m, const float *d_points, int64_t n, flo
     if (o.max_depth < 0) { set_error("max_depth < 0"); return SAND_EINVAL; }
     if (!o.full_depth && m->map_level < 0) { set_error("no depth map loaded"); return SAND_ENOMAP; }
     if (o.full_depth && o.d_exit_layers) { set_error("exit layers are not produced in full-depth mode"); return SAND_EINVAL; }
+    if (o.full_depth && d_count) { set_error("full-depth mode needs a host point count"); return SAND_EINVAL; }
     const bool simt = o.precision == SAND_FP32_SIMT || d_grad != nullptr;
     if (!simt && !tc_supported(m->desc, o.precision)) {
         set_error("precision %d is not supported for this model on the tensor-core path", o.precision);
@@ -389,8 +388,9 @@ static sand_status run_query(sand_model m, const float *d_points, int64_t n, flo
     SAND_CUDA(launch_init_header(ws, s), "workspace reset");
     if (!o.full_depth) {
         MapDev map{m->d_grid, m->d_far, m->map_level, m->desc.n_layers};
-        SAND_CUDA(launch_lookup(map, d_points, n, o.max_depth, d_out, d_grad, o.d_exit_layers, ws, s), "lookup kernel");
-        SAND_CUDA(launch_scatter(d_points, n, m->desc.n_layers, ws, s), "scatter kernel");
+        SAND_CUDA(launch_lookup(map, d_points, n, o.max_depth, d_out, d_grad, o.d_exit_layers, ws, s, d_count),
+                  "lookup kernel");
+        SAND_CUDA(launch_scatter(d_points, n, m->desc.n_layers, ws, s, d_count), "scatter kernel");
     }
     if (ev) SAND_CUDA(cudaEventRecord(ev[1], s), "event record");
     if (simt) {
@@ -404,6 +404,37 @@ static sand_status run_query(sand_model m, const float *d_points, int64_t n, flo
     if (ev) SAND_CUDA(cudaEventRecord(ev[2], s), "event record");
     return SAND_OK;
 }
+
+}  // extern "C"
+
+namespace sand {
+sand_status query_device_count(sand_model m, const float *d_points, int64_t n, const uint32_t *d_count, float *d_out,
+                               float *d_grad, const sand_query_opts *opts, cudaStream_t s) {
+    if (!d_count || !opts || !opts->d_workspace || opts->full_depth) {
+        set_error("device-count query needs a count, a workspace and SAND mode");
+        return SAND_EINVAL;
+    }
+    return run_query(m, d_points, n, d_out, d_grad, opts, s, d_count);
+}
+
+sand_status model_trace_buffer(sand_model m, size_t bytes, void **out) {
+    if (m->trace_bytes < bytes) {
+        cudaFree(m->d_trace);
+        m->d_trace = nullptr;
+        m->trace_bytes = 0;
+        if (cudaMalloc(&m->d_trace, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cannot allocate %zu bytes of sphere-tracer state", bytes);
+            return SAND_ENOMEM;
+        }
+        m->trace_bytes = bytes;
+    }
+    *out = m->d_trace;
+    return SAND_OK;
+}
+}  // namespace sand
+
+extern "C" {
 
 sand_status sand_query_sdf(sand_model m, const float *d_points, int64_t n, float *d_out, const sand_query_opts *opts,
                            void *stream) {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <stdint.h>
 
 #include "sand.h"
@@ -112,11 +113,19 @@ __device__ __forceinline__ float fourier_phase(const float *Bk, float x, float y
 // ---------------------------------------------------------------- host helpers
 void set_error(const char *fmt, ...);
 sand_status cuda_fail(cudaError_t e, const char *what);
+// Return the status of a failed CUDA runtime call from the enclosing function.
+#define SAND_CUDA(call, what)                              \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
 
-// Kernel launchers (stream-ordered, no host synchronisation).
+// Kernel launchers (stream-ordered, no host synchronisation).  With d_count set, the
+// lookup and scatter grids are sized for n points but process min(n, *d_count).
 cudaError_t launch_lookup(const MapDev &map, const float *pts, int64_t n, int max_depth, float *out, float *grad,
-                          uint8_t *exit_layers, void *ws, cudaStream_t s);
-cudaError_t launch_scatter(const float *pts, int64_t n, int n_layers, void *ws, cudaStream_t s);
+                          uint8_t *exit_layers, void *ws, cudaStream_t s, const uint32_t *d_count = nullptr);
+cudaError_t launch_scatter(const float *pts, int64_t n, int n_layers, void *ws, cudaStream_t s,
+                           const uint32_t *d_count = nullptr);
 cudaError_t launch_tmlp_simt(const TmlpDev &M, const float *pts, int64_t n, int full_depth, void *ws,
                              float *out, float *grad, int num_sms, cudaStream_t s);
 cudaError_t launch_init_header(void *ws, cudaStream_t s);
@@ -126,5 +135,11 @@ int model_device(sand_model m);
 bool model_has_map(sand_model m);
 bool model_precision_ready(sand_model m, int precision);  // device weights for `precision` exist already
 sand_status model_prepare(sand_model m, int precision);   // pack device weights for `precision` (may allocate)
+// A SAND query of min(n, *d_count) points whose count is produced on the device (buffers
+// sized for n); opts->d_workspace must hold ws_layout(n).  Full-depth mode is not offered.
+sand_status query_device_count(sand_model m, const float *d_points, int64_t n, const uint32_t *d_count, float *d_out,
+                               float *d_grad, const sand_query_opts *opts, cudaStream_t s);
+// Grow-only device buffer owned by the model for the sphere tracer (stream-ordered reuse).
+sand_status model_trace_buffer(sand_model m, size_t bytes, void **out);
 
 }  // namespace sand

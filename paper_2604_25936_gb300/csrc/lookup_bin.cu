@@ -39,9 +39,11 @@ __device__ __forceinline__ void stage_points(float *sp, const float *pts, int64_
 __global__ void __launch_bounds__(kLookupThreads)
 lookup_kernel(MapDev map, const float *__restrict__ pts, int64_t n, int64_t per_block, int max_depth,
               float *__restrict__ out, float *__restrict__ grad, uint8_t *__restrict__ exit_ws,
-              uint8_t *__restrict__ exit_user, WsHeader *hdr, uint32_t *__restrict__ hist, int n_blocks, int vec) {
+              uint8_t *__restrict__ exit_user, WsHeader *hdr, uint32_t *__restrict__ hist, int n_blocks, int vec,
+              const uint32_t *__restrict__ d_count) {
     __shared__ __align__(16) float sp[kLookupChunk * 3];
     __shared__ uint32_t cnt[16];
+    if (d_count) n = min(n, (int64_t)*d_count);  // point count produced on the device (grid sized for the maximum)
     if (threadIdx.x < 16) cnt[threadIdx.x] = 0;
     const int R = 1 << map.level;
     const int half = R >> 1;
@@ -124,7 +126,9 @@ __global__ void __launch_bounds__(1024) scan_kernel(WsHeader *hdr, uint32_t *his
 
 __global__ void __launch_bounds__(kLookupThreads)
 scatter_kernel(const float *__restrict__ pts, int64_t n, int64_t per_block, const uint8_t *__restrict__ exit_ws,
-               const uint32_t *__restrict__ hist, int n_blocks, int L, float4 *__restrict__ sorted, int vec) {
+               const uint32_t *__restrict__ hist, int n_blocks, int L, float4 *__restrict__ sorted, int vec,
+               const uint32_t *__restrict__ d_count) {
+    if (d_count) n = min(n, (int64_t)*d_count);
     __shared__ __align__(16) float sp[kLookupChunk * 3];
     __shared__ uint32_t base[16], wcnt[kLookupThreads / 32][16], wpre[kLookupThreads / 32][16], tot[16];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -180,7 +184,7 @@ static void lookup_grid(int64_t n, int *g, int64_t *per_block) {
 cudaError_t launch_init_header(void *ws, cudaStream_t s) { return cudaMemsetAsync(ws, 0, sizeof(WsHeader), s); }
 
 cudaError_t launch_lookup(const MapDev &map, const float *pts, int64_t n, int max_depth, float *out, float *grad,
-                          uint8_t *exit_layers, void *ws, cudaStream_t s) {
+                          uint8_t *exit_layers, void *ws, cudaStream_t s, const uint32_t *d_count) {
     WsLayout L = ws_layout(n);
     char *base = static_cast<char *>(ws);
     int g;
@@ -190,11 +194,11 @@ cudaError_t launch_lookup(const MapDev &map, const float *pts, int64_t n, int ma
     lookup_kernel<<<g, kLookupThreads, 0, s>>>(map, pts, n, per, max_depth, out, grad,
                                                reinterpret_cast<uint8_t *>(base + L.exit), exit_layers,
                                                reinterpret_cast<WsHeader *>(base), reinterpret_cast<uint32_t *>(base + L.hist),
-                                               g, vec);
+                                               g, vec, d_count);
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter(const float *pts, int64_t n, int n_layers, void *ws, cudaStream_t s) {
+cudaError_t launch_scatter(const float *pts, int64_t n, int n_layers, void *ws, cudaStream_t s, const uint32_t *d_count) {
     WsLayout L = ws_layout(n);
     char *base = static_cast<char *>(ws);
     int g;
@@ -207,7 +211,7 @@ cudaError_t launch_scatter(const float *pts, int64_t n, int n_layers, void *ws, 
     if (e != cudaSuccess) return e;
     scatter_kernel<<<g, kLookupThreads, 0, s>>>(pts, n, per, reinterpret_cast<const uint8_t *>(base + L.exit),
                                                 reinterpret_cast<const uint32_t *>(base + L.hist), g, n_layers,
-                                                reinterpret_cast<float4 *>(base + L.sorted), vec);
+                                                reinterpret_cast<float4 *>(base + L.sorted), vec, d_count);
     return cudaGetLastError();
 }
 

@@ -32,6 +32,11 @@
 //   SPLIT16  a = a_hi + a_lo and w*s = w_hi + w_lo with fp16 terms (s = 2^-e per
 //            layer, so max|w s| is in [0.5, 1)); D = A_hi B_hi + A_lo B_hi + A_hi B_lo.
 //   F16/BF16 one product with fp16 (scaled) / bf16 operands.
+//   FP8      one product (tcgen05 kind::f8f6f4) with e4m3 operands: weights scaled
+//            per layer by a power of two so max|w s| is in [128, 256); the sine
+//            activations in [-1, 1] are stored unscaled (below 2^-6 the e4m3
+//            subnormal spacing 2^-9 is finer than the normal-range rounding).
+//            A weight stage then holds 128 K-units and an MMA consumes 32.
 // Sine: the argument is formed in revolutions, t = acc * w0/(2 pi s) + w0 b/(2 pi)
 // (one rounding, like forming it in radians), reduced exactly, f = t - rint(t), and
 // the hardware sine is applied to 2 pi f in [-pi, pi].
@@ -46,7 +51,7 @@
 
 namespace sand {
 
-enum TcMode { TC_SPLIT16 = 0, TC_F16 = 1, TC_BF16 = 2 };
+enum TcMode { TC_SPLIT16 = 0, TC_F16 = 1, TC_BF16 = 2, TC_FP8 = 3 };
 
 constexpr int kEpiWarps = 16;
 constexpr int kTcThreads = 64 + 32 * kEpiWarps;
@@ -64,7 +69,7 @@ constexpr int kMiscBytes = kNumBars * 8 + 16 + 3 * 2 * 128 * 4;
 struct TcParams {
     int L, W, D, tail_kind, act, enc, m;
     int first_mma;            // 1-based index of the first layer computed on the tensor cores
-    int kpad;                 // padded K of the packed weight matrix (multiple of 64)
+    int kpad;                 // padded K of the packed weight matrix (multiple of 64; of 128 in the FP8 mode)
     int n_stages;
     uint32_t stage_bytes;     // W * 128
     uint32_t tmem_cols;       // power of two >= W + parts * W / 2
@@ -150,13 +155,23 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b,
 }
 // D[128 x N] (+)= A[128 x 16] . B[N x 16]^T with A read from TMEM (lane = row, 32-bit
 // column = two consecutive fp16/bf16 K-elements).
+template <int MODE>
 __device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
+    if (MODE == TC_FP8) {  // 32 e4m3 K-elements per row, four to a TMEM column
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+    }
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -195,6 +210,11 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *v) {
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t *v) {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr), "r"(v[0]),
                  "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t *v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(v[0]), "r"(v[1]),
+                 "r"(v[2]), "r"(v[3])
                  : "memory");
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
@@ -240,6 +260,13 @@ __device__ __forceinline__ void pack2(float a, float b, uint32_t &hi, uint32_t &
     }
 }
 
+// Four activations -> four e4m3 bytes of one 32-bit TMEM column (first element lowest).
+__device__ __forceinline__ uint32_t pack4_e4m3(float a, float b, float c, float d) {
+    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+    return lo | (hi << 16);
+}
+
 template <int CH>
 __device__ __forceinline__ void tmem_ld_ch(uint32_t taddr, uint32_t *r) {
     if (CH == 32) tmem_ld32(taddr, r);
@@ -258,7 +285,7 @@ template <int MODE, int ACT, int TAIL>
 __device__ __forceinline__ void epilogue16(const float *cs, int W, float c1, const uint32_t *v, int c0, bool write_a,
                                            uint32_t a_hi, uint32_t a_lo, float &sa, float &sb) {
     constexpr bool MULT = TAIL == SAND_TAIL_MULT;
-    uint32_t phi[8], plo[8];
+    uint32_t phi[8], plo[8], p8[4];
 #pragma unroll
     for (int g = 0; g < 2; ++g) {
         const int j0 = c0 + 8 * g;
@@ -283,12 +310,21 @@ __device__ __forceinline__ void epilogue16(const float *cs, int W, float c1, con
             sa = fmaf(av[i], hv, sa);
             if (MULT) sb = fmaf(tbv[i], hv, sb);
         }
+        if (MODE == TC_FP8) {
+            p8[2 * g] = pack4_e4m3(h8[0], h8[1], h8[2], h8[3]);
+            p8[2 * g + 1] = pack4_e4m3(h8[4], h8[5], h8[6], h8[7]);
+        } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) pack2<MODE>(h8[2 * i], h8[2 * i + 1], phi[4 * g + i], plo[4 * g + i]);
+            for (int i = 0; i < 4; ++i) pack2<MODE>(h8[2 * i], h8[2 * i + 1], phi[4 * g + i], plo[4 * g + i]);
+        }
     }
     if (write_a) {
-        tmem_st8(a_hi + (uint32_t)(c0 >> 1), phi);
-        if (MODE == TC_SPLIT16) tmem_st8(a_lo + (uint32_t)(c0 >> 1), plo);
+        if (MODE == TC_FP8) {
+            tmem_st4(a_hi + (uint32_t)(c0 >> 2), p8);
+        } else {
+            tmem_st8(a_hi + (uint32_t)(c0 >> 1), phi);
+            if (MODE == TC_SPLIT16) tmem_st8(a_lo + (uint32_t)(c0 >> 1), plo);
+        }
     }
 }
 
@@ -298,6 +334,8 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                const float4 *__restrict__ sorted, WsHeader *hdr, int64_t n, int full_depth, float *__restrict__ out) {
     constexpr int PARTS = MODE == TC_SPLIT16 ? 2 : 1;
     constexpr bool MULT = TAIL == SAND_TAIL_MULT;
+    constexpr int UPS = MODE == TC_FP8 ? 128 : 64;  // K-units per weight stage (one 128-byte row per unit)
+    constexpr int UPK = MODE == TC_FP8 ? 32 : 16;   // K-units per MMA (32 bytes of every row)
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int W = P.W, L = P.L;
@@ -365,7 +403,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
                 const int Dt = tile_depth(t);
                 for (int l = P.first_mma; l <= Dt && ok; ++l) {
-                    const int kb_n = ((l == 1 ? P.D : W) + 63) >> 6;
+                    const int kb_n = ((l == 1 ? P.D : W) + UPS - 1) / UPS;
                     for (int kb = 0; kb < kb_n && ok; ++kb)
                         for (int p = 0; p < PARTS && ok; ++p, ++it) {
                             const uint32_t s = it % P.n_stages, ph = (it / P.n_stages) & 1;
@@ -375,7 +413,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                             const int row0 = ((l - P.first_mma) * PARTS + p) * W;
                             for (int bx = 0; bx < W; bx += P.box_rows)  // one box of W rows, or two of W/2
                                 tma_load_2d(smem_u32(stage_base + (size_t)s * P.stage_bytes + (size_t)bx * 128), &wmap,
-                                            smem_u32(&full_bar[s]), kb * 64, row0 + bx);
+                                            smem_u32(&full_bar[s]), kb * UPS, row0 + bx);
                         }
                 }
             }
@@ -409,13 +447,11 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                         if (!ok) break;
                     }
                     any_layer = true;
-                    const int kb_n = ((l == 1 ? P.D : W) + 63) >> 6;
-                    const int ks_n = (l == 1 ? P.D : W) >> 4;
+                    const int K = l == 1 ? P.D : W;
+                    const int kb_n = (K + UPS - 1) / UPS;
+                    const int ks_n = (K + UPK - 1) / UPK;  // the last FP8 K-step may be half zero padding
+                    int e_seen = -1;  // last 64-unit block of the A operand waited for in this layer
                     for (int kb = 0; kb < kb_n && ok; ++kb) {
-                        ok = mbar_wait(smem_u32(&a_ready[kb]), pa[kb], abort, hdr, 2, true);
-                        pa[kb] ^= 1;
-                        if (!ok) break;
-                        tc_fence_after();
                         for (int p = 0; p < PARTS && ok; ++p, ++it) {
                             const uint32_t s = it % P.n_stages, ph = (it / P.n_stages) & 1;
                             ok = mbar_wait(smem_u32(&full_bar[s]), ph, abort, hdr, 3, true);
@@ -426,25 +462,33 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                             for (int ks = 0; ks < 4; ++ks) {
                                 const int g = kb * 4 + ks;
                                 if (g >= ks_n) break;  // zero padding of the last K-block
+                                const int e = (g * UPK) >> 6;  // block of the A operand this K-step reads
+                                if (e > e_seen) {
+                                    ok = mbar_wait(smem_u32(&a_ready[e]), pa[e], abort, hdr, 2, true);
+                                    pa[e] ^= 1;
+                                    e_seen = e;
+                                    if (!ok) break;
+                                    tc_fence_after();
+                                }
                                 const uint64_t bd = smem_desc(b_addr + ks * 32);
-                                const uint32_t acol = (uint32_t)g * 8u;  // 16 fp16 K-elements = 8 TMEM columns
+                                const uint32_t acol = (uint32_t)g * 8u;  // 16 fp16 or 32 e4m3 K-elements = 8 TMEM columns
                                 if (p == 0) {
-                                    mma_ts(tmem, a_hi + acol, bd, idesc0, g != 0);
-                                    if (PARTS == 2) mma_ts(tmem, a_lo + acol, bd, idesc0, 1);
+                                    mma_ts<MODE>(tmem, a_hi + acol, bd, idesc0, g != 0);
+                                    if (PARTS == 2) mma_ts<MODE>(tmem, a_lo + acol, bd, idesc0, 1);
                                 } else {
-                                    mma_ts(tmem, a_hi + acol, bd, idesc0, 1);
+                                    mma_ts<MODE>(tmem, a_hi + acol, bd, idesc0, 1);
                                 }
                                 if (n1 > 0) {  // units n0 .. W-1: B rows from n0 on, accumulator columns from n0 on
                                     const uint64_t bd1 = smem_desc(b_addr + (uint32_t)n0 * 128u + ks * 32);
                                     if (p == 0) {
-                                        mma_ts(tmem + (uint32_t)n0, a_hi + acol, bd1, idesc1, g != 0);
-                                        if (PARTS == 2) mma_ts(tmem + (uint32_t)n0, a_lo + acol, bd1, idesc1, 1);
+                                        mma_ts<MODE>(tmem + (uint32_t)n0, a_hi + acol, bd1, idesc1, g != 0);
+                                        if (PARTS == 2) mma_ts<MODE>(tmem + (uint32_t)n0, a_lo + acol, bd1, idesc1, 1);
                                     } else {
-                                        mma_ts(tmem + (uint32_t)n0, a_hi + acol, bd1, idesc1, 1);
+                                        mma_ts<MODE>(tmem + (uint32_t)n0, a_hi + acol, bd1, idesc1, 1);
                                     }
                                 }
                             }
-                            mma_commit(smem_u32(&empty_bar[s]));
+                            if (ok) mma_commit(smem_u32(&empty_bar[s]));
                         }
                     }
                     if (ok) mma_commit(smem_u32(d_full));
@@ -494,7 +538,15 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                 mbar_arrive(smem_u32(x_empty));
             }
         };
+        uint32_t q8[4];  // FP8: units c0-8 .. c0+7 (16-unit groups) go out as one 4-column store
         auto st_a8 = [&](int c0, const float *h8) {  // 8 activations of units c0..c0+7 into TMEM
+            if (MODE == TC_FP8) {  // c0 runs over both halves of an aligned 16-unit group, low half first
+                const int o = (c0 & 8) >> 2;
+                q8[o] = pack4_e4m3(h8[0], h8[1], h8[2], h8[3]);
+                q8[o + 1] = pack4_e4m3(h8[4], h8[5], h8[6], h8[7]);
+                if (o) tmem_st4(a_hi_l + (uint32_t)((c0 - 8) >> 2), q8);
+                return;
+            }
             uint32_t phi[4], plo[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) pack2<MODE>(h8[2 * i], h8[2 * i + 1], phi[i], plo[i]);
@@ -506,6 +558,11 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                              "r"(plo[0]), "r"(plo[1]), "r"(plo[2]), "r"(plo[3])
                              : "memory");
         };
+        if (MODE == TC_FP8 && (W & 31) == 16 && slice == 0) {
+            // units W .. W+15 of the last FP8 K-step meet zero weights; they must hold finite values
+            const uint32_t z[4] = {0u, 0u, 0u, 0u};
+            tmem_st4(a_hi_l + (uint32_t)(W >> 2), z);
+        }
         for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
             const int Dt = tile_depth(t);
             const int64_t row = t * kTileM + r;

@@ -2,6 +2,7 @@
 // launch configuration.  The kernel is in tc_kernel.cuh; one translation unit
 // per precision mode instantiates it (tc_inst_*.cu) so they build in parallel.
 #include <cudaTypedefs.h>
+#include <cuda_fp8.h>
 #include <string.h>
 
 #include <cmath>
@@ -17,6 +18,7 @@ static int mode_of(int precision) {
         case SAND_FP32: return TC_SPLIT16;
         case SAND_FP16: return TC_F16;
         case SAND_BF16: return TC_BF16;
+        case SAND_FP8: return TC_FP8;
         default: return -1;
     }
 }
@@ -27,6 +29,8 @@ bool tc_supported(const sand_tmlp_desc &d, int precision) {
     // width 336: the accumulator (336 columns) plus one fp16 operand (168) fill TMEM; no room for the float32 split
     if (d.width == 336 && mode_of(precision) == TC_SPLIT16) return false;
     if (d.encoder == SAND_ENC_FOURIER && d.in_dim != d.width) return false;
+    // FP8 stores the activations unscaled, which holds for the sine's [-1, 1] only
+    if (mode_of(precision) == TC_FP8 && d.activation != SAND_ACT_SINE) return false;
     return d.n_layers >= 1;
 }
 
@@ -69,7 +73,10 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
     const bool sine = d.activation == SAND_ACT_SINE;
     const int first = d.encoder == SAND_ENC_FOURIER ? 1 : 2;
     const int parts = mode == TC_SPLIT16 ? 2 : 1;
-    const int kpad = (W + 63) / 64 * 64;  // K padded with zero weights to whole K-blocks
+    const bool fp8 = mode == TC_FP8;
+    const int eb = fp8 ? 1 : 2;                   // bytes per packed weight
+    const int ups = fp8 ? 128 : 64;               // K-units per 128-byte weight row of a stage
+    const int kpad = (W + ups - 1) / ups * ups;   // K padded with zero weights to whole stages
     const int n_mma = L - first + 1;
     const float *p = params;
     const float *B = nullptr;
@@ -84,7 +91,7 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
 
     // packed hidden-layer weights, rows [(li * parts + part) * W + unit][k]
     const size_t rows = (size_t)(n_mma > 0 ? n_mma : 1) * parts * W;
-    std::vector<uint16_t> packed(rows * kpad, 0);
+    std::vector<uint8_t> packed(rows * kpad * eb, 0);
     std::vector<float> c1(kMaxLayers, 1.f);
     for (int li = 0; li < n_mma; ++li) {
         const int l = first + li;
@@ -96,12 +103,18 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
         if (mode != TC_BF16 && amax > 0.f) {
             int e;
             frexpf(amax, &e);      // amax = f 2^e, f in [0.5, 1)
-            s = ldexpf(1.f, -e);   // amax s in [0.5, 1); a power of two, so the scaling is exact
+            // amax s in [0.5, 1) (fp16) or [128, 256) (e4m3, largest finite 448); a power of two, so exact
+            s = ldexpf(1.f, fp8 ? 8 - e : -e);
         }
         c1[l - 1] = (float)(turn / (double)s);
         for (int nr = 0; nr < W; ++nr)
             for (int k = 0; k < K; ++k) {
                 const float w = Wl[(size_t)nr * K + k] * s;
+                const size_t at = ((size_t)(li * parts) * W + nr) * kpad + k;
+                if (fp8) {
+                    packed[at] = (uint8_t)__nv_cvt_float_to_fp8(w, __NV_SATFINITE, __NV_E4M3);
+                    continue;
+                }
                 uint16_t hi, lo = 0;
                 if (mode == TC_BF16) {
                     __nv_bfloat16 b = __float2bfloat16_rn(w);
@@ -114,8 +127,8 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
                         memcpy(&lo, &l2, 2);
                     }
                 }
-                packed[((size_t)(li * parts) * W + nr) * kpad + k] = hi;
-                if (parts == 2) packed[((size_t)(li * parts + 1) * W + nr) * kpad + k] = lo;
+                memcpy(&packed[at * 2], &hi, 2);
+                if (parts == 2) memcpy(&packed[(at + (size_t)W * kpad) * 2], &lo, 2);
             }
     }
     // per-layer constants [L][3][W]: bias' (omega0 b / 2 pi for sine), tail a, tail b; first layer [3][W]
@@ -133,13 +146,13 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
     if (first == 2)
         for (int k = 0; k < 3; ++k)
             for (int j = 0; j < W; ++j) w1p[(size_t)k * W + j] = (float)(turn * (double)W1[(size_t)j * 3 + k]);
-    const size_t off_c = (packed.size() * 2 + 255) / 256 * 256;
+    const size_t off_c = (packed.size() + 255) / 256 * 256;
     const size_t off_w1 = off_c + cvec.size() * 4;
     const size_t off_tb = off_w1 + w1p.size() * 4;
     const size_t off_B = off_tb + tbv.size() * 4;
     const size_t total = off_B + (size_t)mf * 3 * 4 + 16;
     std::vector<uint8_t> blob(total, 0);
-    memcpy(blob.data(), packed.data(), packed.size() * 2);
+    memcpy(blob.data(), packed.data(), packed.size());
     memcpy(blob.data() + off_c, cvec.data(), cvec.size() * 4);
     memcpy(blob.data() + off_w1, w1p.data(), w1p.size() * 4);
     memcpy(blob.data() + off_tb, tbv.data(), tbv.size() * 4);
@@ -168,11 +181,12 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
         return SAND_EUNSUPPORTED;
     }
     cuuint64_t gdim[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
-    cuuint64_t gstride[1] = {(cuuint64_t)kpad * 2};
+    cuuint64_t gstride[1] = {(cuuint64_t)kpad * eb};
     const int box_rows = W <= 256 ? W : W / 2;
-    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    cuuint32_t box[2] = {(cuuint32_t)ups, (cuuint32_t)box_rows};  // 128 bytes per row: the swizzle span
     cuuint32_t estride[2] = {1, 1};
-    CUresult cr = enc(&pk->map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, dbuf, gdim, gstride, box, estride,
+    CUresult cr = enc(&pk->map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, dbuf, gdim,
+                      gstride, box, estride,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (cr != CUDA_SUCCESS) {
@@ -188,8 +202,9 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
     P.stage_bytes = (uint32_t)W * 128u;
     P.box_rows = box_rows;
     P.n_split = W <= 256 ? W : 176;
-    {   // accumulator (W columns) + A_hi (W/2) [+ A_lo (W/2)], rounded up to a power of two
-        uint32_t need = (uint32_t)W + (uint32_t)parts * (uint32_t)(W / 2), cols = 32;
+    {   // accumulator (W columns) + A_hi (W/2; FP8: ceil32(W)/4) [+ A_lo (W/2)], rounded up to a power of two
+        const uint32_t a_cols = fp8 ? (uint32_t)((W + 31) / 32 * 8) : (uint32_t)(W / 2);
+        uint32_t need = (uint32_t)W + (uint32_t)parts * a_cols, cols = 32;
         while (cols < need) cols <<= 1;
         P.tmem_cols = cols;
     }
@@ -238,6 +253,9 @@ cudaError_t launch_tmlp_tc(const TcModel &tc, const TmlpDev &M, const float *pts
                                               smem, s);
         case TC_F16:
             return launch_tc_mode<TC_F16>(pk->map, P, P.act, P.tail_kind, pts, sorted, hdr, n, full_depth, out, grid, smem,
+                                          s);
+        case TC_FP8:
+            return launch_tc_mode<TC_FP8>(pk->map, P, P.act, P.tail_kind, pts, sorted, hdr, n, full_depth, out, grid, smem,
                                           s);
         default:
             return launch_tc_mode<TC_BF16>(pk->map, P, P.act, P.tail_kind, pts, sorted, hdr, n, full_depth, out, grid, smem,

@@ -1,0 +1,123 @@
+"""FP8 (e4m3) hidden-layer products on the tensor cores, against the FP64 oracle.
+
+e4m3 keeps 3 mantissa bits (unit roundoff 2^-4), so the FP8 mode is an
+approximation whose error is reported, not bounded by the float32 tolerance.
+The bounds here come from emulating the same quantisation (per-layer
+power-of-two weight scale, unscaled sine activations, float32 accumulation)
+in float64 on 20,000 uniform points: for the 8 x 256 and 8 x 336 SIRENs the
+error at exit layer 8 is 2.6e-2 max and 5.7e-3 RMS (4 x 64: 1.3e-2 / 3.0e-3).
+The tests allow 3x the emulated maximum and 2x the emulated RMS.  Points that
+exit at layer 1 never touch the tensor cores (layer 1 is float32), so they
+keep the float32 tolerance, and exit layers stay bit-exact.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+MAX_TOL = 0.08
+RMS_TOL = 0.012
+
+
+def load(model, tree=None):
+    from paper_2604_25936_gb300 import Model
+    m = Model.from_params(*model.header_ints(), model.omega0, model.flat(), device=0)
+    if tree is not None:
+        m.set_depth_map(tree.max_level, tree.n_layers, tree.child, tree.depth, tree.far)
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def check_fp8(y_gpu, y_ref, d_ref=None, what=""):
+    y = y_gpu.double().cpu().numpy() if isinstance(y_gpu, torch.Tensor) else np.asarray(y_gpu, np.float64)
+    assert np.isfinite(y).all(), what + ": non-finite output"
+    err = np.abs(y - y_ref)
+    if d_ref is not None:
+        one = d_ref == 1
+        if one.any():
+            assert err[one].max() <= 1e-5, "%s: exit-layer-1 rows |err| %.3g" % (what, err[one].max())
+        zero = d_ref == 0
+        if zero.any():
+            assert err[zero].max() == 0 or err[zero].max() <= 1e-7, what + ": far leaves changed"
+    rms = float(np.sqrt((err ** 2).mean())) if err.size else 0.0
+    assert err.max() <= MAX_TOL, "%s: max |err| %.3g (bound %g)" % (what, err.max(), MAX_TOL)
+    assert rms <= RMS_TOL, "%s: rms err %.3g (bound %g)" % (what, rms, RMS_TOL)
+    return float(err.max()), rms
+
+
+def test_fp8_tiny():
+    model, tree, pts = synth.config_tiny()
+    m = load(model, tree)
+    y_ref, d_ref = oracle.query(model, tree, pts, exit_layers=True)
+    y, el = m.query(dev(pts), precision="fp8", exit_layers=True)
+    np.testing.assert_array_equal(el.cpu().numpy().astype(np.int32), d_ref)
+    check_fp8(y, y_ref, d_ref, "tiny/fp8")
+    m.free()
+
+
+@pytest.mark.parametrize("tail", [synth.TAIL_LINEAR, synth.TAIL_MULT])
+def test_fp8_scene(tail):
+    """8 x 256 SIREN on its level-7 octree (64^3 lattice), full depth, LOD clamps, far leaves."""
+    model = synth.siren_tmlp(8, 256, seed=1, tail_kind=tail)
+    tree = synth.scene_octree(7, 8, far_field=tail == synth.TAIL_MULT)
+    m = load(model, tree)
+    pts = synth.lattice(64)
+    for lod in (0, 3):
+        y_ref, d_ref = oracle.query(model, tree, pts, max_depth=lod, exit_layers=True)
+        y, el = m.query(dev(pts), precision="fp8", max_depth=lod, exit_layers=True)
+        np.testing.assert_array_equal(el.cpu().numpy().astype(np.int32), d_ref)
+        check_fp8(y, y_ref, d_ref, "scene64/fp8/lod%d" % lod)
+    full = synth.uniform_points(20001, seed=17)
+    check_fp8(m.query(dev(full), precision="fp8", full_depth=True), oracle.full_depth(model, full), None, "full/fp8")
+    g = np.random.Generator(np.random.PCG64(3))
+    for n in (1, 127, 129, 4097):
+        p = g.uniform(-1, 1, (n, 3)).astype(np.float32)
+        check_fp8(m.query(dev(p), precision="fp8"), oracle.query(model, tree, p), None, "n=%d" % n)
+    m.free()
+
+
+def test_fp8_width_336():
+    """The wide variant: two MMA column groups and a last K-step half zero padding."""
+    model = synth.siren_tmlp(8, 336, seed=2)
+    tree = synth.scene_octree(7, 8, transform=synth.rotation([0, 1, 0], 0.5), scale=0.95)
+    m = load(model, tree)
+    pts = synth.lattice(48)
+    y_ref, d_ref = oracle.query(model, tree, pts, exit_layers=True)
+    y, el = m.query(dev(pts), precision="fp8", exit_layers=True)
+    np.testing.assert_array_equal(el.cpu().numpy().astype(np.int32), d_ref)
+    check_fp8(y, y_ref, d_ref, "w336/fp8")
+    full = synth.uniform_points(3001, seed=19)
+    check_fp8(m.query(dev(full), precision="fp8", full_depth=True), oracle.full_depth(model, full), None,
+              "w336 full/fp8")
+    m.free()
+
+
+def test_fp8_full_size_sampled():
+    """256^3 lattice in the benchmark's launch configuration; error on 20,000 sampled points."""
+    model = synth.siren_tmlp(8, 256, seed=1)
+    tree = synth.scene_octree(7, 8)
+    m = load(model, tree)
+    pts = synth.lattice(256)
+    y, el = m.query(dev(pts), precision="fp8", exit_layers=True, workspace=m.workspace(len(pts)))
+    d_ref, _ = oracle.lookup(tree, pts)
+    np.testing.assert_array_equal(el.cpu().numpy().astype(np.int32), d_ref)
+    idx = synth.sample_indices(len(pts), 20000, seed=11)
+    check_fp8(y.cpu().numpy()[idx], oracle.query(model, tree, pts[idx]), d_ref[idx], "256^3 sampled/fp8")
+    m.free()
+
+
+def test_fp8_rejects_relu():
+    """FP8 stores activations unscaled, valid for the sine's [-1, 1] only: ReLU models are refused."""
+    from paper_2604_25936_gb300 import SandError
+    model = synth.relu_ff_tmlp(6, 128, n_freq=64, sigma=10.0, seed=3)
+    m = load(model)
+    with pytest.raises(SandError, match="EUNSUPPORTED"):
+        m.query(dev(synth.uniform_points(100, 1)), precision="fp8", full_depth=True)
+    m.free()
