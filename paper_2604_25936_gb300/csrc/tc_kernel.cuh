@@ -37,9 +37,12 @@
 //            activations in [-1, 1] are stored unscaled (below 2^-6 the e4m3
 //            subnormal spacing 2^-9 is finer than the normal-range rounding).
 //            A weight stage then holds 128 K-units and an MMA consumes 32.
-// Sine: the argument is formed in revolutions, t = acc * w0/(2 pi s) + w0 b/(2 pi)
-// (one rounding, like forming it in radians), reduced exactly, f = t - rint(t), and
-// the hardware sine is applied to 2 pi f in [-pi, pi].
+// Sine: the argument is formed in radians with one rounding, u = acc * w0/s + w0 b, and
+// passed to the hardware sine, which takes it to revolutions (one more rounding,
+// relative 2^-24) and reduces it there; for the |u| < 64 of these networks that adds
+// under 4e-6 rad to the phase, against the 1e-5 output tolerance.  An explicit exact
+// reduction first costs three more instructions per unit, and the epilogue's
+// instruction count sets the layer time.
 // Every mbarrier wait is bounded (2 s of %globaltimer); on timeout the CTA sets
 // SAND_FLAG_TIMEOUT, stops issuing work, drains its copies and MMAs, frees TMEM
 // and returns.
@@ -75,9 +78,9 @@ struct TcParams {
     uint32_t tmem_cols;       // power of two >= W + parts * W / 2
     int box_rows;             // rows per TMA box: W, or W / 2 when W > 256 (box dimensions are at most 256)
     int n_split;              // first MMA column group when W > 256 (a multiple of 16)
-    float c1[kMaxLayers];     // per layer: w0 / (2 pi s) (sine) or 1 / s (ReLU)
-    const float *cvec;        // [L][3][W]: bias' (w0 b / 2 pi for sine, b for ReLU), tail a, tail b
-    const float *w1p;         // [3][W] first-layer weights (times w0 / 2 pi for sine), transposed
+    float c1[kMaxLayers];     // per layer: w0 / s (sine) or 1 / s (ReLU)
+    const float *cvec;        // [L][3][W]: bias' (w0 b for sine, b for ReLU), tail a, tail b
+    const float *w1p;         // [3][W] first-layer weights (times w0 for sine), transposed
     const float *B;           // [m][3] Fourier matrix
     const float *tb;          // [L][2] tail biases
 };
@@ -173,6 +176,52 @@ __device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_
             : "memory");
     }
 }
+// Runs of MMAs in one asm statement: K-step k reads A at a + 8k TMEM columns and B at
+// descriptor b + 2k (32 bytes further in every 128-byte row).  Measured on GB300, the
+// single issuing thread keeps the tensor pipe full (one M=128, N=256 MMA per 128 cycles)
+// only when a stage's MMAs leave it as one straight run like this; one asm statement
+// per MMA, with the address arithmetic between them, issues at 150-190 cycles per MMA.
+// The first MMA accumulates iff acc; the rest always do.
+#define SAND_MMA_K4(KIND)                                                                                  \
+    asm volatile("{\n\t.reg .pred p, t;\n\t.reg .b64 b1, b2, b3;\n\t.reg .b32 a1, a2, a3;\n\t"              \
+                 "setp.ne.b32 p, %4, 0;\n\tsetp.ne.b32 t, %3, 0;\n\t"                                       \
+                 "add.s64 b1, %2, 2;\n\tadd.s64 b2, %2, 4;\n\tadd.s64 b3, %2, 6;\n\t"                       \
+                 "add.s32 a1, %1, 8;\n\tadd.s32 a2, %1, 16;\n\tadd.s32 a3, %1, 24;\n\t"                     \
+                 KIND " [%0], [%1], %2, %3, p;\n\t" KIND " [%0], [a1], b1, %3, t;\n\t"                        \
+                 KIND " [%0], [a2], b2, %3, t;\n\t" KIND " [%0], [a3], b3, %3, t;\n\t}"                       \
+                 ::"r"(d), "r"(a), "l"(b), "r"(idesc), "r"(acc) : "memory")
+#define SAND_MMA_K2(KIND)                                                                                  \
+    asm volatile("{\n\t.reg .pred p, t;\n\t.reg .b64 b1;\n\t.reg .b32 a1;\n\t"                             \
+                 "setp.ne.b32 p, %4, 0;\n\tsetp.ne.b32 t, %3, 0;\n\t"                                       \
+                 "add.s64 b1, %2, 2;\n\tadd.s32 a1, %1, 8;\n\t"                                            \
+                 KIND " [%0], [%1], %2, %3, p;\n\t" KIND " [%0], [a1], b1, %3, t;\n\t}"                        \
+                 ::"r"(d), "r"(a), "l"(b), "r"(idesc), "r"(acc) : "memory")
+#define SAND_KIND_F16 "tcgen05.mma.cta_group::1.kind::f16"
+#define SAND_KIND_F8 "tcgen05.mma.cta_group::1.kind::f8f6f4"
+template <int MODE>
+__device__ __forceinline__ void mma_k4(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if (MODE == TC_FP8) SAND_MMA_K4(SAND_KIND_F8);
+    else SAND_MMA_K4(SAND_KIND_F16);
+}
+template <int MODE>
+__device__ __forceinline__ void mma_k2(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if (MODE == TC_FP8) SAND_MMA_K2(SAND_KIND_F8);
+    else SAND_MMA_K2(SAND_KIND_F16);
+}
+// Four K-steps, each with two A operands against the same B (the float32 mode's
+// A_hi B_hi and A_lo B_hi products).
+__device__ __forceinline__ void mma_k4x2(uint32_t d, uint32_t a, uint32_t a2, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n\t.reg .pred p, t;\n\t.reg .b64 b1, b2, b3;\n\t.reg .b32 a1, q1, a2_, q2, a3, q3;\n\t"
+                 "setp.ne.b32 p, %5, 0;\n\tsetp.ne.b32 t, %4, 0;\n\t"
+                 "add.s64 b1, %3, 2;\n\tadd.s64 b2, %3, 4;\n\tadd.s64 b3, %3, 6;\n\t"
+                 "add.s32 a1, %1, 8;\n\tadd.s32 a2_, %1, 16;\n\tadd.s32 a3, %1, 24;\n\t"
+                 "add.s32 q1, %2, 8;\n\tadd.s32 q2, %2, 16;\n\tadd.s32 q3, %2, 24;\n\t"
+                 SAND_KIND_F16 " [%0], [%1], %3, %4, p;\n\t" SAND_KIND_F16 " [%0], [%2], %3, %4, t;\n\t"
+                 SAND_KIND_F16 " [%0], [a1], b1, %4, t;\n\t" SAND_KIND_F16 " [%0], [q1], b1, %4, t;\n\t"
+                 SAND_KIND_F16 " [%0], [a2_], b2, %4, t;\n\t" SAND_KIND_F16 " [%0], [q2], b2, %4, t;\n\t"
+                 SAND_KIND_F16 " [%0], [a3], b3, %4, t;\n\t" SAND_KIND_F16 " [%0], [q3], b3, %4, t;\n\t}"
+                 ::"r"(d), "r"(a), "r"(a2), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -227,16 +276,10 @@ __device__ __forceinline__ int tc_row_depth(const WsHeader *hdr, uint32_t r, int
     return d;
 }
 
-// sin(2 pi t) for a phase t in revolutions: exact reduction to [-1/2, 1/2], then the hardware sine.
-__device__ __forceinline__ float sin_rev(float t) {
-    const float f = t - rintf(t);
-    return __sinf(f * 6.28318530717958647692f);
-}
-
 template <int ACT>
 __device__ __forceinline__ float activate(float t) {
     if (ACT == SAND_ACT_RELU) return fmaxf(t, 0.f);
-    return sin_rev(t);
+    return __sinf(t);
 }
 
 // Two activations -> one packed 16-bit pair (low half = first element) and, in the
@@ -340,7 +383,6 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int W = P.W, L = P.L;
     const int KB = (W + 63) >> 6;   // K-blocks of 64 units (the last one partial when W % 64 != 0)
-    const int KS = W >> 4;          // K-steps of 16 holding real units
     const bool drain_first = (W & 63) == 0 && KB <= 4;  // else: serial epilogue (see below)
     uint8_t *stage_base = smem;
     float *dbuf = reinterpret_cast<float *>(stage_base + (size_t)P.n_stages * P.stage_bytes);  // [(KB-2)*16][512]
@@ -457,12 +499,14 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                             ok = mbar_wait(smem_u32(&full_bar[s]), ph, abort, hdr, 3, true);
                             if (!ok) break;
                             tc_fence_after();
-                            const uint32_t b_addr = smem_u32(stage_base + (size_t)s * P.stage_bytes);
-#pragma unroll
-                            for (int ks = 0; ks < 4; ++ks) {
-                                const int g = kb * 4 + ks;
-                                if (g >= ks_n) break;  // zero padding of the last K-block
-                                const int e = (g * UPK) >> 6;  // block of the A operand this K-step reads
+                            const uint64_t bd = smem_desc(smem_u32(stage_base + (size_t)s * P.stage_bytes));
+                            const int nks = min(4, ks_n - kb * 4);  // K-steps of this stage holding real units
+                            // runs of K-steps that read one 64-unit block of the A operand: the whole
+                            // stage (16-bit operands), or halves of it (FP8: 128 units per stage)
+                            constexpr int SEG = MODE == TC_FP8 ? 2 : 4;
+                            for (int g0 = 0; g0 < nks && ok; g0 += SEG) {
+                                const int g = kb * 4 + g0;
+                                const int e = (g * UPK) >> 6;  // block of the A operand these K-steps read
                                 if (e > e_seen) {
                                     ok = mbar_wait(smem_u32(&a_ready[e]), pa[e], abort, hdr, 2, true);
                                     pa[e] ^= 1;
@@ -470,21 +514,27 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                                     if (!ok) break;
                                     tc_fence_after();
                                 }
-                                const uint64_t bd = smem_desc(b_addr + ks * 32);
+                                const int cnt = min(SEG, nks - g0);
                                 const uint32_t acol = (uint32_t)g * 8u;  // 16 fp16 or 32 e4m3 K-elements = 8 TMEM columns
-                                if (p == 0) {
-                                    mma_ts<MODE>(tmem, a_hi + acol, bd, idesc0, g != 0);
-                                    if (PARTS == 2) mma_ts<MODE>(tmem, a_lo + acol, bd, idesc0, 1);
-                                } else {
-                                    mma_ts<MODE>(tmem, a_hi + acol, bd, idesc0, 1);
-                                }
-                                if (n1 > 0) {  // units n0 .. W-1: B rows from n0 on, accumulator columns from n0 on
-                                    const uint64_t bd1 = smem_desc(b_addr + (uint32_t)n0 * 128u + ks * 32);
-                                    if (p == 0) {
-                                        mma_ts<MODE>(tmem + (uint32_t)n0, a_hi + acol, bd1, idesc1, g != 0);
-                                        if (PARTS == 2) mma_ts<MODE>(tmem + (uint32_t)n0, a_lo + acol, bd1, idesc1, 1);
-                                    } else {
-                                        mma_ts<MODE>(tmem + (uint32_t)n0, a_hi + acol, bd1, idesc1, 1);
+                                const uint32_t acc = (p != 0 || g != 0) ? 1u : 0u;
+                                const uint32_t a_op = a_hi + acol;
+                                for (int grp = 0; grp < (n1 > 0 ? 2 : 1); ++grp) {
+                                    // column group grp: accumulator columns and B rows from n0 on for grp 1
+                                    const uint32_t dcol = grp ? tmem + (uint32_t)n0 : tmem;
+                                    const uint32_t id = grp ? idesc1 : idesc0;
+                                    const uint64_t bk = bd + (uint64_t)(2 * g0) + (grp ? (uint64_t)n0 * 8u : 0u);
+                                    if (PARTS == 2 && p == 0 && cnt == 4) {
+                                        mma_k4x2(dcol, a_op, a_lo + acol, bk, id, acc);
+                                    } else if (cnt == 4) {
+                                        mma_k4<MODE>(dcol, a_op, bk, id, acc);
+                                    } else if (cnt == 2 && PARTS == 1) {
+                                        mma_k2<MODE>(dcol, a_op, bk, id, acc);
+                                    } else {  // a ragged last stage: one K-step at a time
+                                        for (int k = 0; k < cnt; ++k) {
+                                            const uint32_t ak = k == 0 ? acc : 1u;
+                                            mma_ts<MODE>(dcol, a_op + 8u * k, bk + 2u * k, id, ak);
+                                            if (PARTS == 2 && p == 0) mma_ts<MODE>(dcol, a_lo + acol + 8u * k, bk + 2u * k, id, 1u);
+                                        }
                                     }
                                 }
                             }
@@ -545,18 +595,18 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                 q8[o] = pack4_e4m3(h8[0], h8[1], h8[2], h8[3]);
                 q8[o + 1] = pack4_e4m3(h8[4], h8[5], h8[6], h8[7]);
                 if (o) tmem_st4(a_hi_l + (uint32_t)((c0 - 8) >> 2), q8);
-                return;
-            }
-            uint32_t phi[4], plo[4];
+            } else {
+                uint32_t phi[4], plo[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) pack2<MODE>(h8[2 * i], h8[2 * i + 1], phi[i], plo[i]);
-            asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_hi_l + (uint32_t)(c0 >> 1)),
-                         "r"(phi[0]), "r"(phi[1]), "r"(phi[2]), "r"(phi[3])
-                         : "memory");
-            if (MODE == TC_SPLIT16)
-                asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_lo_l + (uint32_t)(c0 >> 1)),
-                             "r"(plo[0]), "r"(plo[1]), "r"(plo[2]), "r"(plo[3])
+                for (int i = 0; i < 4; ++i) pack2<MODE>(h8[2 * i], h8[2 * i + 1], phi[i], plo[i]);
+                asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_hi_l + (uint32_t)(c0 >> 1)),
+                             "r"(phi[0]), "r"(phi[1]), "r"(phi[2]), "r"(phi[3])
                              : "memory");
+                if (MODE == TC_SPLIT16)
+                    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_lo_l + (uint32_t)(c0 >> 1)),
+                                 "r"(plo[0]), "r"(plo[1]), "r"(plo[2]), "r"(plo[3])
+                                 : "memory");
+            }
         };
         if (MODE == TC_FP8 && (W & 31) == 16 && slice == 0) {
             // units W .. W+15 of the last FP8 K-step meet zero weights; they must hold finite values

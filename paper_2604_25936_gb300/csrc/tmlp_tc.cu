@@ -87,7 +87,7 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
     const float *bh = p; p += (size_t)(L - 1) * W;
     const float *tw = p; p += (size_t)L * 2 * W;
     const float *tbias = p;
-    const double turn = sine ? (double)d.omega0 / (2.0 * M_PI) : 1.0;  // omega0 / (2 pi): phase in revolutions
+    const double turn = sine ? (double)d.omega0 : 1.0;  // omega0 folded into the constants: phase in radians
 
     // packed hidden-layer weights, rows [(li * parts + part) * W + unit][k]
     const size_t rows = (size_t)(n_mma > 0 ? n_mma : 1) * parts * W;
@@ -131,7 +131,7 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
                 if (parts == 2) memcpy(&packed[(at + (size_t)W * kpad) * 2], &lo, 2);
             }
     }
-    // per-layer constants [L][3][W]: bias' (omega0 b / 2 pi for sine), tail a, tail b; first layer [3][W]
+    // per-layer constants [L][3][W]: bias' (omega0 b for sine), tail a, tail b; first layer [3][W]
     std::vector<float> cvec((size_t)L * 3 * W, 0.f), w1p((size_t)3 * W, 0.f), tbv((size_t)L * 2);
     for (int l = 1; l <= L; ++l) {
         const float *bl = l == 1 ? b1 : bh + (size_t)(l - 2) * W;
