@@ -720,20 +720,37 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                     signal(d_drained, false);
                 } else {
                 // drain the accumulator: K-blocks 0-1 to registers, 2-3 (if any) through shared memory
+                // ([block][quarter][thread] float4s, conflict-free); the loads of K-blocks 1 and 3 are
+                // in flight while K-block 0 is computed, and the next layer starts once both are done
                 const int et = threadIdx.x - 64;
-                uint32_t v0[16], v1[16];
-                tmem_ld16(t_lane + (uint32_t)(16 * slice), v0);
-                if (KB > 1) tmem_ld16(t_lane + (uint32_t)(64 + 16 * slice), v1);
-                for (int kb = 2; kb < KB; ++kb) {
-                    uint32_t tmp[16];
-                    tmem_ld16(t_lane + (uint32_t)(64 * kb + 16 * slice), tmp);
-                    tmem_wait_ld();
+                float4 *dbuf4 = reinterpret_cast<float4 *>(dbuf);
+                auto stash = [&](int kb, const uint32_t *tv) {
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) dbuf[((kb - 2) * 16 + i) * kEpiThreads + et] = __uint_as_float(tmp[i]);
+                    for (int j = 0; j < 4; ++j)
+                        dbuf4[((kb - 2) * 4 + j) * kEpiThreads + et] =
+                            make_float4(__uint_as_float(tv[4 * j]), __uint_as_float(tv[4 * j + 1]),
+                                        __uint_as_float(tv[4 * j + 2]), __uint_as_float(tv[4 * j + 3]));
+                };
+                uint32_t v0[16], v1[16];
+                if (KB > 2) {
+                    uint32_t t2[16], t3[16];
+                    tmem_ld16(t_lane + (uint32_t)(16 * slice), v0);
+                    tmem_ld16(t_lane + (uint32_t)(128 + 16 * slice), t2);
+                    tmem_wait_ld();
+                    stash(2, t2);
+                    tmem_ld16(t_lane + (uint32_t)(64 + 16 * slice), v1);
+                    tmem_ld16(t_lane + (uint32_t)(192 + 16 * slice), t3);
+                    epilogue16<MODE, ACT, TAIL>(cs, W, c1, v0, 16 * slice, !last, a_hi_l, a_lo_l, sa, sb);
+                    tmem_wait_ld();
+                    stash(3, t3);
+                    signal(d_drained, false);  // the next layer may overwrite the accumulator
+                } else {
+                    tmem_ld16(t_lane + (uint32_t)(16 * slice), v0);
+                    if (KB > 1) tmem_ld16(t_lane + (uint32_t)(64 + 16 * slice), v1);
+                    tmem_wait_ld();
+                    signal(d_drained, false);
+                    epilogue16<MODE, ACT, TAIL>(cs, W, c1, v0, 16 * slice, !last, a_hi_l, a_lo_l, sa, sb);
                 }
-                tmem_wait_ld();
-                signal(d_drained, false);  // the next layer may overwrite the accumulator
-                epilogue16<MODE, ACT, TAIL>(cs, W, c1, v0, 16 * slice, !last, a_hi_l, a_lo_l, sa, sb);
                 if (!last) signal(&a_ready[0], true);
                 if (KB > 1) {
                     epilogue16<MODE, ACT, TAIL>(cs, W, c1, v1, 64 + 16 * slice, !last, a_hi_l, a_lo_l, sa, sb);
@@ -742,7 +759,11 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                 for (int kb = 2; kb < KB; ++kb) {
                     uint32_t tmp[16];
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) tmp[i] = __float_as_uint(dbuf[((kb - 2) * 16 + i) * kEpiThreads + et]);
+                    for (int j = 0; j < 4; ++j) {
+                        const float4 q = dbuf4[((kb - 2) * 4 + j) * kEpiThreads + et];
+                        tmp[4 * j] = __float_as_uint(q.x); tmp[4 * j + 1] = __float_as_uint(q.y);
+                        tmp[4 * j + 2] = __float_as_uint(q.z); tmp[4 * j + 3] = __float_as_uint(q.w);
+                    }
                     epilogue16<MODE, ACT, TAIL>(cs, W, c1, tmp, 64 * kb + 16 * slice, !last, a_hi_l, a_lo_l, sa, sb);
                     if (!last) signal(&a_ready[kb], true);
                 }
