@@ -477,29 +477,37 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             const uint32_t id_base = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(kTileM >> 4) << 24);
             const uint32_t idesc0 = id_base | ((uint32_t)(n0 >> 3) << 17);
             const uint32_t idesc1 = id_base | ((uint32_t)(n1 >> 3) << 17);
-            uint32_t it = 0, pdr = 0;
+            // At a layer boundary the tensor pipe is idle until this thread issues again, and the
+            // epilogue warps sharing its SM sub-partition are busy then, so every instruction
+            // between the accumulator's release and the first MMA counts: the stage ring position
+            // is kept as running counters (no division), and the first weight stage of a layer is
+            // waited for before the accumulator is (its copy landed long before).
+            uint32_t s = 0, ph = 0, pdr = 0;
+            const uint64_t bd_base = smem_desc(smem_u32(stage_base));
+            const uint64_t bd_step = (uint64_t)(P.stage_bytes >> 4);  // descriptor units per stage
             uint32_t pa[kMaxKBlocks] = {0, 0, 0, 0, 0, 0};
             bool ok = true, any_layer = false;
             for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
                 const int Dt = tile_depth(t);
                 for (int l = P.first_mma; l <= Dt && ok; ++l) {
+                    const int K = l == 1 ? P.D : W;
+                    const int kb_n = (K + UPS - 1) / UPS;
+                    const int ks_n = (K + UPK - 1) / UPK;  // the last FP8 K-step may be half zero padding
+                    int e_seen = -1;  // last 64-unit block of the A operand waited for in this layer
+                    ok = mbar_wait(smem_u32(&full_bar[s]), ph, abort, hdr, 3, true);
+                    if (!ok) break;
                     if (any_layer) {  // the previous layer's accumulator has been read out
                         ok = mbar_wait(smem_u32(d_drained), pdr, abort, hdr, 8, true);
                         pdr ^= 1;
                         if (!ok) break;
                     }
                     any_layer = true;
-                    const int K = l == 1 ? P.D : W;
-                    const int kb_n = (K + UPS - 1) / UPS;
-                    const int ks_n = (K + UPK - 1) / UPK;  // the last FP8 K-step may be half zero padding
-                    int e_seen = -1;  // last 64-unit block of the A operand waited for in this layer
                     for (int kb = 0; kb < kb_n && ok; ++kb) {
-                        for (int p = 0; p < PARTS && ok; ++p, ++it) {
-                            const uint32_t s = it % P.n_stages, ph = (it / P.n_stages) & 1;
-                            ok = mbar_wait(smem_u32(&full_bar[s]), ph, abort, hdr, 3, true);
+                        for (int p = 0; p < PARTS && ok; ++p) {
+                            if (kb + p > 0) ok = mbar_wait(smem_u32(&full_bar[s]), ph, abort, hdr, 3, true);
                             if (!ok) break;
                             tc_fence_after();
-                            const uint64_t bd = smem_desc(smem_u32(stage_base + (size_t)s * P.stage_bytes));
+                            const uint64_t bd = bd_base + (uint64_t)s * bd_step;
                             const int nks = min(4, ks_n - kb * 4);  // K-steps of this stage holding real units
                             // runs of K-steps that read one 64-unit block of the A operand: the whole
                             // stage (16-bit operands), or halves of it (FP8: 128 units per stage)
@@ -539,6 +547,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                                 }
                             }
                             if (ok) mma_commit(smem_u32(&empty_bar[s]));
+                            if (++s == (uint32_t)P.n_stages) { s = 0; ph ^= 1; }
                         }
                     }
                     if (ok) mma_commit(smem_u32(d_full));
