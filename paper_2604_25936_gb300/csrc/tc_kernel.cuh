@@ -1,15 +1,15 @@
 // Tensor-core T-MLP kernel for sm_103a (tcgen05 MMA, TMEM accumulators, TMA).
 //
 // Evaluates Eq. 2 (and Eq. 3 for multiplicative tails) for 128-row tiles of
-// points sorted by descending exit layer.  One persistent CTA per SM, 576 threads:
+// points sorted by descending exit layer.  One persistent CTA per SM, 320 threads:
 //   warp 0       TMA producer: streams weight tiles (64 K-columns x W units, one
 //                K-block of one layer) from L2 into a ring of stages, 128-byte
 //                swizzled (the K-major layout the MMA reads).
 //   warp 1       owns TMEM and issues tcgen05.mma from one thread:
 //                D[128 x W] (fp32, TMEM) += A[128 x 16] . B[W x 16]^T, A read from TMEM.
-//   warps 2..17  epilogue.  Thread (quadrant q, lane i) owns tile row 32 q + i (the
-//                TMEM lane restriction); the four warps of a quadrant take a quarter
-//                of the units each.  Layer 1 (float32, on the CUDA cores), bias,
+//   warps 2..9   epilogue.  Thread (quadrant q, lane i) owns tile row 32 q + i (the
+//                TMEM lane restriction); the two warps of a quadrant take half of the
+//                units of every K-block each.  Layer 1 (float32, on the CUDA cores), bias,
 //                sine, tails, the running sum y_l = y_{l-1} + t_l and the write at
 //                each row's exit layer.  The new activations are packed to fp16 and
 //                written with tcgen05.st into TMEM, where the next layer's MMAs read
@@ -19,11 +19,13 @@
 // issuing thread sustains about one M=128 MMA per 140-165 cycles whatever N is, so
 // N = 256 is what reaches the tensor cores' rate.
 // Overlap of a layer's epilogue with the next layer's MMAs: each epilogue thread
-// first loads all of its accumulator columns into registers and signals d_drained
-// (the next layer may now overwrite D), then produces the next A operand one
-// K-block (64 units) at a time, signalling a_ready[kb] after each; the MMAs of the
-// next layer on K-block kb start as soon as a_ready[kb] completes.  Thread
-// (quadrant, slice s) owns units 64 kb + 16 s .. + 15 of every K-block kb.
+// first loads all of its accumulator columns into registers (128 at W = 256) and
+// signals d_drained (the next layer may now overwrite D), then produces the next A
+// operand one K-block (64 units) at a time, signalling a_ready[kb] after each; the
+// MMAs of the next layer on K-block kb start as soon as a_ready[kb] completes.
+// Thread (quadrant, slice s) owns units 64 kb + 32 s .. + 31 of every K-block kb.
+// Two epilogue warps per SM sub-partition (not four) leave the MMA-issuing thread
+// issue slots when it is on the critical path, and 200 registers per thread.
 // A tile runs to the exit layer of its first (deepest) row; rows whose exit layer
 // was reached ride along only in the one tile per exit layer that straddles two
 // layers; tiles of exit layer 1 never touch the tensor cores.
@@ -56,7 +58,9 @@ namespace sand {
 
 enum TcMode { TC_SPLIT16 = 0, TC_F16 = 1, TC_BF16 = 2, TC_FP8 = 3 };
 
-constexpr int kEpiWarps = 16;
+constexpr int kSlices = 2;                  // epilogue warps per TMEM lane quadrant
+constexpr int kSliceUnits = 64 / kSlices;   // units of every 64-unit K-block per epilogue thread
+constexpr int kEpiWarps = 4 * kSlices;
 constexpr int kTcThreads = 64 + 32 * kEpiWarps;
 constexpr int kTileM = 128;
 constexpr int kEpiThreads = 32 * kEpiWarps;
@@ -65,13 +69,22 @@ constexpr int kSmemBudget = 227 * 1024;
 constexpr int kMaxStages = 8;
 constexpr int kMaxKBlocks = 6;  // K padded to a multiple of 64, W <= 336
 constexpr int kNumBars = 2 * kMaxStages + kMaxKBlocks + 5;  // full, empty, a_ready[kb], d_full, d_drained, drain, x_full, x_empty
+// An epilogue thread's row of a tile: coordinates, exit layer, original index (-1: padding).
+struct TcRow {
+    float x0, x1, x2;
+    int d;
+    int64_t idx;
+};
 // bytes after the weight stages and constants: barriers, TMEM slot + abort flag,
-// tail exchange (3 slices x 2 values x 128 rows)
-constexpr int kMiscBytes = kNumBars * 8 + 16 + 3 * 2 * 128 * 4;
+// tail exchange ((kSlices - 1) slices x 2 values x 128 rows)
+constexpr int kMiscBytes = kNumBars * 8 + 16 + (kSlices - 1) * 2 * 128 * 4;
+static_assert(kSlices == 2, "the epilogue loads 32 accumulator columns per K-block and thread");
 
 struct TcParams {
     int L, W, D, tail_kind, act, enc, m;
-    int first_mma;            // 1-based index of the first layer computed on the tensor cores
+    int first_mma;            // 1-based index of the first layer computed on the tensor cores (1)
+    int l1_fold;              // layer 1 is one K = 16 fp16 MMA over split coordinates (not Fourier features)
+    float x_scale;            // coordinates are scaled by this before the split
     int kpad;                 // padded K of the packed weight matrix (multiple of 64; of 128 in the FP8 mode)
     int n_stages;
     uint32_t stage_bytes;     // W * 128
@@ -80,7 +93,6 @@ struct TcParams {
     int n_split;              // first MMA column group when W > 256 (a multiple of 16)
     float c1[kMaxLayers];     // per layer: w0 / s (sine) or 1 / s (ReLU)
     const float *cvec;        // [L][3][W]: bias' (w0 b for sine, b for ReLU), tail a, tail b
-    const float *w1p;         // [3][W] first-layer weights (times w0 for sine), transposed
     const float *B;           // [m][3] Fourier matrix
     const float *tb;          // [L][2] tail biases
 };
@@ -247,24 +259,25 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r) {
         : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-// registers -> TMEM, 16 or 8 consecutive 32-bit columns of this thread's lane.
+// registers -> TMEM, 16, 8 or 4 consecutive 32-bit columns of this thread's lane.  No
+// "memory" clobber: the store touches no memory the compiler tracks, so shared-memory loads
+// of the next chunk may be scheduled above it; volatile asm keeps its order relative to
+// the tcgen05.wait::st that publishes it.
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *v) {
     asm volatile(
         "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
         "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
         "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
         "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
-        : "memory");
+       );
 }
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t *v) {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr), "r"(v[0]),
-                 "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
-                 : "memory");
+                 "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]));
 }
 __device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t *v) {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(v[0]), "r"(v[1]),
-                 "r"(v[2]), "r"(v[3])
-                 : "memory");
+                 "r"(v[2]), "r"(v[3]));
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
@@ -385,9 +398,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
     const int KB = (W + 63) >> 6;   // K-blocks of 64 units (the last one partial when W % 64 != 0)
     const bool drain_first = (W & 63) == 0 && KB <= 4;  // else: serial epilogue (see below)
     uint8_t *stage_base = smem;
-    float *dbuf = reinterpret_cast<float *>(stage_base + (size_t)P.n_stages * P.stage_bytes);  // [(KB-2)*16][512]
-    float *c_l1 = dbuf + (size_t)(drain_first && KB > 2 ? KB - 2 : 0) * 16 * kEpiThreads;      // [3][W] first-layer weights
-    float *c_all = c_l1 + 3 * W;                                                                // [L][3][W]
+    float *c_all = reinterpret_cast<float *>(stage_base + (size_t)P.n_stages * P.stage_bytes);  // [L][3][W]
     uint64_t *bars = reinterpret_cast<uint64_t *>(c_all + (size_t)3 * L * W);
     uint64_t *full_bar = bars;
     uint64_t *empty_bar = bars + kMaxStages;
@@ -395,11 +406,11 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
     uint64_t *d_full = a_ready + kMaxKBlocks;   // the layer's accumulator is complete
     uint64_t *d_drained = d_full + 1;           // every epilogue warp has read the accumulator (16 warps)
     uint64_t *drain = d_drained + 1;
-    uint64_t *x_full = drain + 1;   // tail partials of slices 1-3 written (384 arrivals)
+    uint64_t *x_full = drain + 1;   // tail partials of slice 1 written (128 arrivals)
     uint64_t *x_empty = x_full + 1; // ... and read by slice 0 (128 arrivals)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + kNumBars);
     volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
-    float *tailx = reinterpret_cast<float *>(tmem_slot + 4);  // [3 slices][2 values][128 rows]
+    float *tailx = reinterpret_cast<float *>(tmem_slot + 4);  // [kSlices - 1][2 values][128 rows]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n_rows = full_depth ? n : (int64_t)hdr->n_active;
@@ -415,7 +426,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
         mbar_init(smem_u32(d_full), 1);
         mbar_init(smem_u32(d_drained), kEpiWarps);
         mbar_init(smem_u32(drain), 1);
-        mbar_init(smem_u32(x_full), 3 * 128);
+        mbar_init(smem_u32(x_full), (kSlices - 1) * 128);
         mbar_init(smem_u32(x_empty), 128);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -428,8 +439,6 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
     }
     if (warp >= 2) {  // constants of every layer, resident for the whole kernel
         for (int i = threadIdx.x - 64; i < 3 * L * W; i += kEpiThreads) c_all[i] = __ldg(P.cvec + i);
-        if (P.first_mma == 2)
-            for (int i = threadIdx.x - 64; i < 3 * W; i += kEpiThreads) c_l1[i] = __ldg(P.w1p + i);
     }
     tc_fence_before();
     __syncthreads();
@@ -446,8 +455,9 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                 const int Dt = tile_depth(t);
                 for (int l = P.first_mma; l <= Dt && ok; ++l) {
                     const int kb_n = ((l == 1 ? P.D : W) + UPS - 1) / UPS;
+                    const int parts_l = (l == 1 && P.l1_fold) ? 1 : PARTS;  // the folded layer 1 has one block
                     for (int kb = 0; kb < kb_n && ok; ++kb)
-                        for (int p = 0; p < PARTS && ok; ++p, ++it) {
+                        for (int p = 0; p < parts_l && ok; ++p, ++it) {
                             const uint32_t s = it % P.n_stages, ph = (it / P.n_stages) & 1;
                             ok = mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1, abort, hdr, 1, true);
                             if (!ok) break;
@@ -477,6 +487,9 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             const uint32_t id_base = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(kTileM >> 4) << 24);
             const uint32_t idesc0 = id_base | ((uint32_t)(n0 >> 3) << 17);
             const uint32_t idesc1 = id_base | ((uint32_t)(n1 >> 3) << 17);
+            const uint32_t id_l1 = (1u << 4) | ((uint32_t)(kTileM >> 4) << 24);  // fp16 operands, fp32 accumulate
+            const uint32_t idesc0_l1 = id_l1 | ((uint32_t)(n0 >> 3) << 17);
+            const uint32_t idesc1_l1 = id_l1 | ((uint32_t)(n1 >> 3) << 17);
             // At a layer boundary the tensor pipe is idle until this thread issues again, and the
             // epilogue warps sharing its SM sub-partition are busy then, so every instruction
             // between the accumulator's release and the first MMA counts: the stage ring position
@@ -502,8 +515,10 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                         if (!ok) break;
                     }
                     any_layer = true;
+                    const bool fold = l == 1 && P.l1_fold;
+                    const int parts_l = fold ? 1 : PARTS;
                     for (int kb = 0; kb < kb_n && ok; ++kb) {
-                        for (int p = 0; p < PARTS && ok; ++p) {
+                        for (int p = 0; p < parts_l && ok; ++p) {
                             if (kb + p > 0) ok = mbar_wait(smem_u32(&full_bar[s]), ph, abort, hdr, 3, true);
                             if (!ok) break;
                             tc_fence_after();
@@ -526,6 +541,11 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                                 const uint32_t acol = (uint32_t)g * 8u;  // 16 fp16 or 32 e4m3 K-elements = 8 TMEM columns
                                 const uint32_t acc = (p != 0 || g != 0) ? 1u : 0u;
                                 const uint32_t a_op = a_hi + acol;
+                                if (fold) {  // layer 1: one fp16 K-step per column group, whatever the mode
+                                    mma_ts<TC_F16>(tmem, a_op, bd, idesc0_l1, 0u);
+                                    if (n1 > 0) mma_ts<TC_F16>(tmem + (uint32_t)n0, a_op, bd + (uint64_t)n0 * 8u, idesc1_l1, 0u);
+                                    continue;
+                                }
                                 for (int grp = 0; grp < (n1 > 0 ? 2 : 1); ++grp) {
                                     // column group grp: accumulator columns and B rows from n0 on for grp 1
                                     const uint32_t dcol = grp ? tmem + (uint32_t)n0 : tmem;
@@ -562,9 +582,10 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
         }
         __syncwarp();
     } else {
-        // ------------------------------------------------ epilogue warps 2..17
+        // ------------------------------------------------ epilogue warps 2..9
         const int q = warp & 3;                 // TMEM lane quadrant
-        const int slice = (warp - 2) >> 2;      // 16-unit slice of every K-block
+        const int slice = (warp - 2) >> 2;      // which half of every K-block
+        const int su0 = kSliceUnits * slice;    // first unit of this thread in every K-block
         const int r = q * 32 + lane;            // tile row
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
         const uint32_t t_lane = tmem + lane_off;
@@ -577,7 +598,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(bar));
         };
-        // Tail exchange through two mbarriers (bounded waits): slices 1-3 publish their
+        // Tail exchange through two mbarriers (bounded waits): slice 1 publishes its
         // partial dot products, slice 0 adds them to its own.
         auto exchange = [&](float &sa, float &sb) {
             if (slice != 0) {
@@ -590,7 +611,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                 ok = mbar_wait(smem_u32(x_full), px, abort, hdr, 7, false) && ok;
                 px ^= 1;
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
+                for (int k = 0; k < kSlices - 1; ++k) {
                     sa += tailx[k * 256 + r];
                     if (MULT) sb += tailx[k * 256 + 128 + r];
                 }
@@ -609,12 +630,10 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
 #pragma unroll
                 for (int i = 0; i < 4; ++i) pack2<MODE>(h8[2 * i], h8[2 * i + 1], phi[i], plo[i]);
                 asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_hi_l + (uint32_t)(c0 >> 1)),
-                             "r"(phi[0]), "r"(phi[1]), "r"(phi[2]), "r"(phi[3])
-                             : "memory");
+                             "r"(phi[0]), "r"(phi[1]), "r"(phi[2]), "r"(phi[3]));
                 if (MODE == TC_SPLIT16)
                     asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_lo_l + (uint32_t)(c0 >> 1)),
-                                 "r"(plo[0]), "r"(plo[1]), "r"(plo[2]), "r"(plo[3])
-                                 : "memory");
+                                 "r"(plo[0]), "r"(plo[1]), "r"(plo[2]), "r"(plo[3]));
             }
         };
         if (MODE == TC_FP8 && (W & 31) == 16 && slice == 0) {
@@ -622,72 +641,69 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             const uint32_t z[4] = {0u, 0u, 0u, 0u};
             tmem_st4(a_hi_l + (uint32_t)(W >> 2), z);
         }
-        for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-            const int Dt = tile_depth(t);
-            const int64_t row = t * kTileM + r;
-            int d = 0;
-            int64_t idx = -1;
-            float x0 = 0.f, x1 = 0.f, x2 = 0.f;
-            if (row < n_rows) {
+        // this thread's row of tile tt: coordinates, exit layer, original index (-1 for padding)
+        auto load_row = [&](int64_t tt) {
+            TcRow a{0.f, 0.f, 0.f, 0, -1};
+            const int64_t row = tt * kTileM + r;
+            if (tt < n_tiles && row < n_rows) {
                 if (full_depth) {
-                    idx = row;
-                    d = L;
-                    x0 = pts[3 * row]; x1 = pts[3 * row + 1]; x2 = pts[3 * row + 2];
+                    a.idx = row;
+                    a.d = L;
+                    a.x0 = pts[3 * row]; a.x1 = pts[3 * row + 1]; a.x2 = pts[3 * row + 2];
                 } else {
                     const float4 v = sorted[row];
-                    x0 = v.x; x1 = v.y; x2 = v.z;
-                    idx = __float_as_int(v.w);
-                    d = tc_row_depth(hdr, (uint32_t)row, L);
+                    a.x0 = v.x; a.x1 = v.y; a.x2 = v.z;
+                    a.idx = __float_as_int(v.w);
+                    a.d = tc_row_depth(hdr, (uint32_t)row, L);
                 }
             }
-            float y = 0.f;
-            const bool write_first = Dt >= P.first_mma;
-            // ---- layer 1 on the CUDA cores (or the Fourier features feeding an MMA layer 1)
-            if (P.first_mma == 2) {
-                float ta = 0.f;
-                const float *b1 = c_all;       // bias' of layer 1
-                const float *a1 = c_all + W;   // tail a of layer 1
-                for (int kb = 0; kb < KB; ++kb) {
-                    for (int c0 = 64 * kb + 16 * slice; c0 < 64 * kb + 16 * slice + 16 && c0 < W; c0 += 8) {
-                        const float4 w0a = *reinterpret_cast<const float4 *>(c_l1 + c0);
-                        const float4 w0b = *reinterpret_cast<const float4 *>(c_l1 + c0 + 4);
-                        const float4 w1a = *reinterpret_cast<const float4 *>(c_l1 + W + c0);
-                        const float4 w1b = *reinterpret_cast<const float4 *>(c_l1 + W + c0 + 4);
-                        const float4 w2a = *reinterpret_cast<const float4 *>(c_l1 + 2 * W + c0);
-                        const float4 w2b = *reinterpret_cast<const float4 *>(c_l1 + 2 * W + c0 + 4);
-                        const float4 ba = *reinterpret_cast<const float4 *>(b1 + c0);
-                        const float4 bb = *reinterpret_cast<const float4 *>(b1 + c0 + 4);
-                        const float4 aa = *reinterpret_cast<const float4 *>(a1 + c0);
-                        const float4 ab4 = *reinterpret_cast<const float4 *>(a1 + c0 + 4);
-                        const float w0v[8] = {w0a.x, w0a.y, w0a.z, w0a.w, w0b.x, w0b.y, w0b.z, w0b.w};
-                        const float w1v[8] = {w1a.x, w1a.y, w1a.z, w1a.w, w1b.x, w1b.y, w1b.z, w1b.w};
-                        const float w2v[8] = {w2a.x, w2a.y, w2a.z, w2a.w, w2b.x, w2b.y, w2b.z, w2b.w};
-                        const float bv[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
-                        const float av[8] = {aa.x, aa.y, aa.z, aa.w, ab4.x, ab4.y, ab4.z, ab4.w};
-                        float h8[8];
+            return a;
+        };
+        // The A operand of a folded layer 1: 256 x = x_h + x_m + x_l exactly (three fp16 parts,
+        // each the rounded residual of the last); K slots [x_h, x_m, x_l, x_h, x_m] x (x, y, z), 0
+        // against the packed weights.  Written by one warp per quadrant, signalled by all.
+        auto put_a1 = [&](const TcRow &a) {
+            if (slice == 0) {
+                const float xs[3] = {a.x0 * P.x_scale, a.x1 * P.x_scale, a.x2 * P.x_scale};
+                __half hp[3][3];
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            float u = fmaf(w0v[i], x0, bv[i]);
-                            u = fmaf(w1v[i], x1, u);
-                            u = fmaf(w2v[i], x2, u);
-                            const float hv = activate<ACT>(u);
-                            h8[i] = hv;
-                            ta = fmaf(av[i], hv, ta);
-                        }
-                        if (write_first) st_a8(c0, h8);
-                    }
-                    if (write_first) signal(&a_ready[kb], true);
+                for (int c = 0; c < 3; ++c) {
+                    const __half h = __float2half_rn(xs[c]);
+                    const float r1 = xs[c] - __half2float(h);
+                    const __half m = __float2half_rn(r1);
+                    const __half lo = __float2half_rn(r1 - __half2float(m));
+                    hp[c][0] = h; hp[c][1] = m; hp[c][2] = lo;
                 }
-                float sb = 0.f;
-                exchange(ta, sb);
-                if (slice == 0) {
-                    y = ta + __ldg(P.tb);
-                    if (d == 1 && idx >= 0) out[idx] = y;
+                __half k16[16];
+#pragma unroll
+                for (int g = 0; g < 5; ++g)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) k16[3 * g + c] = hp[c][g < 3 ? g : g - 3];
+                k16[15] = __float2half_rn(0.f);
+                uint32_t v8[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    __half2 pr = __halves2half2(k16[2 * i], k16[2 * i + 1]);
+                    v8[i] = *reinterpret_cast<uint32_t *>(&pr);
                 }
+                tmem_st8(a_hi_l, v8);
+            }
+            signal(&a_ready[0], true);
+        };
+        for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+            const int Dt = tile_depth(t);
+            const TcRow cur = load_row(t);
+            const int d = cur.d;
+            const int64_t idx = cur.idx;
+            const float x0 = cur.x0, x1 = cur.x1, x2 = cur.x2;
+            float y = 0.f;
+            // ---- the A operand of layer 1: split coordinates, or the Fourier features
+            if (P.l1_fold) {
+                put_a1(cur);
             } else {
                 // Fourier features gamma(x) = [sin 2 pi s, cos 2 pi s]; in_dim == W, same slices as the layers
                 for (int kb = 0; kb < KB; ++kb) {
-                    for (int k0 = 64 * kb + 16 * slice; k0 < 64 * kb + 16 * slice + 16 && k0 < W; k0 += 8) {
+                    for (int k0 = 64 * kb + su0; k0 < 64 * kb + su0 + kSliceUnits && k0 < W; k0 += 8) {
                         float h8[8];
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
@@ -717,8 +733,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                     // serial: each K-block read, computed and stored in turn; the next layer may start
                     // overwriting the accumulator only once every warp has read all of it
                     for (int kb = 0; kb < KB; ++kb) {
-                        const int c0 = 64 * kb + 16 * slice;
-                        if (c0 < W) {
+                        for (int c0 = 64 * kb + su0; c0 < 64 * kb + su0 + kSliceUnits && c0 < W; c0 += 16) {
                             uint32_t v[16];
                             tmem_ld16(t_lane + (uint32_t)c0, v);
                             tmem_wait_ld();
@@ -728,54 +743,28 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                     }
                     signal(d_drained, false);
                 } else {
-                // drain the accumulator: K-blocks 0-1 to registers, 2-3 (if any) through shared memory
-                // ([block][quarter][thread] float4s, conflict-free); the loads of K-blocks 1 and 3 are
-                // in flight while K-block 0 is computed, and the next layer starts once both are done
-                const int et = threadIdx.x - 64;
-                float4 *dbuf4 = reinterpret_cast<float4 *>(dbuf);
-                auto stash = [&](int kb, const uint32_t *tv) {
+                    // drain the accumulator into registers: K-block 0 first, the others load while
+                    // K-block 0 is computed; the next layer starts once all are in
+                    uint32_t v[4][kSliceUnits];
+                    tmem_ld32(t_lane + (uint32_t)su0, v[0]);
+                    tmem_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        dbuf4[((kb - 2) * 4 + j) * kEpiThreads + et] =
-                            make_float4(__uint_as_float(tv[4 * j]), __uint_as_float(tv[4 * j + 1]),
-                                        __uint_as_float(tv[4 * j + 2]), __uint_as_float(tv[4 * j + 3]));
-                };
-                uint32_t v0[16], v1[16];
-                if (KB > 2) {
-                    uint32_t t2[16], t3[16];
-                    tmem_ld16(t_lane + (uint32_t)(16 * slice), v0);
-                    tmem_ld16(t_lane + (uint32_t)(128 + 16 * slice), t2);
+                    for (int kb = 1; kb < 4; ++kb)
+                        if (kb < KB) tmem_ld32(t_lane + (uint32_t)(64 * kb + su0), v[kb]);
+                    epilogue16<MODE, ACT, TAIL>(cs, W, c1, v[0], su0, !last, a_hi_l, a_lo_l, sa, sb);
+                    epilogue16<MODE, ACT, TAIL>(cs, W, c1, v[0] + 16, su0 + 16, !last, a_hi_l, a_lo_l, sa, sb);
                     tmem_wait_ld();
-                    stash(2, t2);
-                    tmem_ld16(t_lane + (uint32_t)(64 + 16 * slice), v1);
-                    tmem_ld16(t_lane + (uint32_t)(192 + 16 * slice), t3);
-                    epilogue16<MODE, ACT, TAIL>(cs, W, c1, v0, 16 * slice, !last, a_hi_l, a_lo_l, sa, sb);
-                    tmem_wait_ld();
-                    stash(3, t3);
                     signal(d_drained, false);  // the next layer may overwrite the accumulator
-                } else {
-                    tmem_ld16(t_lane + (uint32_t)(16 * slice), v0);
-                    if (KB > 1) tmem_ld16(t_lane + (uint32_t)(64 + 16 * slice), v1);
-                    tmem_wait_ld();
-                    signal(d_drained, false);
-                    epilogue16<MODE, ACT, TAIL>(cs, W, c1, v0, 16 * slice, !last, a_hi_l, a_lo_l, sa, sb);
-                }
-                if (!last) signal(&a_ready[0], true);
-                if (KB > 1) {
-                    epilogue16<MODE, ACT, TAIL>(cs, W, c1, v1, 64 + 16 * slice, !last, a_hi_l, a_lo_l, sa, sb);
-                    if (!last) signal(&a_ready[1], true);
-                }
-                for (int kb = 2; kb < KB; ++kb) {
-                    uint32_t tmp[16];
+                    if (!last) signal(&a_ready[0], true);
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const float4 q = dbuf4[((kb - 2) * 4 + j) * kEpiThreads + et];
-                        tmp[4 * j] = __float_as_uint(q.x); tmp[4 * j + 1] = __float_as_uint(q.y);
-                        tmp[4 * j + 2] = __float_as_uint(q.z); tmp[4 * j + 3] = __float_as_uint(q.w);
+                    for (int kb = 1; kb < 4; ++kb) {
+                        if (kb < KB) {
+                            epilogue16<MODE, ACT, TAIL>(cs, W, c1, v[kb], 64 * kb + su0, !last, a_hi_l, a_lo_l, sa, sb);
+                            epilogue16<MODE, ACT, TAIL>(cs, W, c1, v[kb] + 16, 64 * kb + su0 + 16, !last, a_hi_l, a_lo_l,
+                                                        sa, sb);
+                            if (!last) signal(&a_ready[kb], true);
+                        }
                     }
-                    epilogue16<MODE, ACT, TAIL>(cs, W, c1, tmp, 64 * kb + 16 * slice, !last, a_hi_l, a_lo_l, sa, sb);
-                    if (!last) signal(&a_ready[kb], true);
-                }
                 }
                 exchange(sa, sb);
                 if (slice == 0) {

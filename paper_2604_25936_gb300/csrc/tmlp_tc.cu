@@ -54,11 +54,8 @@ struct TcPack {
 
 size_t tc_smem_bytes(const TcParams &P, int parts) {
     (void)parts;  // the A operand lives in TMEM
-    const int kb = (P.W + 63) / 64;
-    const bool drain_first = (P.W % 64) == 0 && kb <= 4;
     return 1024 /*alignment slack*/ + (size_t)P.n_stages * P.stage_bytes +
-           (size_t)(drain_first && kb > 2 ? kb - 2 : 0) * 16 * kEpiThreads * 4 /*accumulator drain buffer*/ +
-           (size_t)4 * (3 * P.W + (size_t)3 * P.L * P.W) /*first-layer weights, per-layer constants*/ + kMiscBytes;
+           (size_t)4 * 3 * P.L * P.W /*per-layer constants*/ + kMiscBytes;
 }
 
 sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params, int precision) {
@@ -71,7 +68,13 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
     tc_release(tc);
     const int L = d.n_layers, W = d.width, D = d.in_dim, mf = d.n_freq;
     const bool sine = d.activation == SAND_ACT_SINE;
-    const int first = d.encoder == SAND_ENC_FOURIER ? 1 : 2;
+    // Layer 1 always runs on the tensor cores.  Fourier features feed it as a W-wide A
+    // operand; raw coordinates feed one K = 16 MMA whose K slots hold the cross terms of a
+    // three-part fp16 split of 256 x (exact for float32 x) and a two-part split of the
+    // weights, which gives float32-class products (fold1).
+    const int first = 1;
+    const bool fold1 = d.encoder != SAND_ENC_FOURIER;
+    const float x_scale = 256.f;  // keeps the smallest coordinate part out of the fp16 subnormals
     const int parts = mode == TC_SPLIT16 ? 2 : 1;
     const bool fp8 = mode == TC_FP8;
     const int eb = fp8 ? 1 : 2;                   // bytes per packed weight
@@ -96,6 +99,34 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
     for (int li = 0; li < n_mma; ++li) {
         const int l = first + li;
         const int K = l == 1 ? D : W;
+        if (l == 1 && fold1) {
+            // B row of unit j (fp16 bits, K = 16): [w_h x3 coords] x 3, [w_l x3] x 2, 0, against
+            // A = [x_h, x_m, x_l, x_h, x_m] (three coordinates each), so the product sums
+            // x_h w_h + x_m w_h + x_l w_h + x_h w_l + x_m w_l
+            float amax = 0.f;
+            for (size_t i = 0; i < (size_t)W * D; ++i) amax = fmaxf(amax, fabsf(W1[i]));
+            float s = 1.f;
+            if (amax > 0.f) {
+                int e;
+                frexpf(amax, &e);
+                s = ldexpf(1.f, -e);
+            }
+            c1[0] = (float)(turn / ((double)s * x_scale));
+            for (int j = 0; j < W; ++j) {
+                uint16_t wh[3], wl[3];
+                for (int k = 0; k < 3; ++k) {
+                    const float w = W1[(size_t)j * 3 + k] * s;
+                    const __half h = __float2half_rn(w);
+                    const __half lo = __float2half_rn(w - __half2float(h));
+                    memcpy(&wh[k], &h, 2);
+                    memcpy(&wl[k], &lo, 2);
+                }
+                uint16_t row[16] = {wh[0], wh[1], wh[2], wh[0], wh[1], wh[2], wh[0], wh[1], wh[2],
+                                    wl[0], wl[1], wl[2], wl[0], wl[1], wl[2], 0};
+                memcpy(&packed[(size_t)j * kpad * eb], row, sizeof row);  // the first 32 bytes of the row
+            }
+            continue;
+        }
         const float *Wl = l == 1 ? W1 : Wh + (size_t)(l - 2) * W * W;
         float amax = 0.f;
         for (size_t i = 0; i < (size_t)W * K; ++i) amax = fmaxf(amax, fabsf(Wl[i]));
@@ -131,8 +162,8 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
                 if (parts == 2) memcpy(&packed[(at + (size_t)W * kpad) * 2], &lo, 2);
             }
     }
-    // per-layer constants [L][3][W]: bias' (omega0 b for sine), tail a, tail b; first layer [3][W]
-    std::vector<float> cvec((size_t)L * 3 * W, 0.f), w1p((size_t)3 * W, 0.f), tbv((size_t)L * 2);
+    // per-layer constants [L][3][W]: bias' (omega0 b for sine), tail a, tail b
+    std::vector<float> cvec((size_t)L * 3 * W, 0.f), tbv((size_t)L * 2);
     for (int l = 1; l <= L; ++l) {
         const float *bl = l == 1 ? b1 : bh + (size_t)(l - 2) * W;
         for (int j = 0; j < W; ++j) {
@@ -143,18 +174,13 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
         tbv[2 * (l - 1)] = tbias[2 * (l - 1)];
         tbv[2 * (l - 1) + 1] = tbias[2 * (l - 1) + 1];
     }
-    if (first == 2)
-        for (int k = 0; k < 3; ++k)
-            for (int j = 0; j < W; ++j) w1p[(size_t)k * W + j] = (float)(turn * (double)W1[(size_t)j * 3 + k]);
     const size_t off_c = (packed.size() + 255) / 256 * 256;
-    const size_t off_w1 = off_c + cvec.size() * 4;
-    const size_t off_tb = off_w1 + w1p.size() * 4;
+    const size_t off_tb = off_c + cvec.size() * 4;
     const size_t off_B = off_tb + tbv.size() * 4;
     const size_t total = off_B + (size_t)mf * 3 * 4 + 16;
     std::vector<uint8_t> blob(total, 0);
     memcpy(blob.data(), packed.data(), packed.size());
     memcpy(blob.data() + off_c, cvec.data(), cvec.size() * 4);
-    memcpy(blob.data() + off_w1, w1p.data(), w1p.size() * 4);
     memcpy(blob.data() + off_tb, tbv.data(), tbv.size() * 4);
     if (B) memcpy(blob.data() + off_B, B, (size_t)mf * 3 * 4);
 
@@ -196,7 +222,7 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
         return SAND_ECUDA;
     }
     TcParams &P = pk->P;
-    P.L = L; P.W = W; P.D = D; P.tail_kind = d.tail_kind; P.act = d.activation; P.enc = d.encoder; P.m = mf;
+    P.L = L; P.W = W; P.D = fold1 ? 16 : D; P.l1_fold = fold1 ? 1 : 0; P.x_scale = x_scale; P.tail_kind = d.tail_kind; P.act = d.activation; P.enc = d.encoder; P.m = mf;
     P.first_mma = first;
     P.kpad = kpad;
     P.stage_bytes = (uint32_t)W * 128u;
@@ -210,7 +236,6 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
     }
     for (int l = 0; l < kMaxLayers; ++l) P.c1[l] = c1[l];
     P.cvec = reinterpret_cast<const float *>(dbuf + off_c);
-    P.w1p = reinterpret_cast<const float *>(dbuf + off_w1);
     P.tb = reinterpret_cast<const float *>(dbuf + off_tb);
     P.B = B ? reinterpret_cast<const float *>(dbuf + off_B) : nullptr;
     P.n_stages = 1;
