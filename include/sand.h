@@ -106,7 +106,9 @@ typedef struct {
     int32_t precision;      /* sand_precision (default SAND_FP32) */
     int32_t max_depth;      /* level of detail (Sec. 3.4): exit layer <- min(d, max_depth) for d > 0; 0 = off */
     int32_t full_depth;     /* 1: ignore the depth map and run every point to layer L (plain T-MLP) */
-    int32_t reserved;
+    int32_t all_tails;      /* with full_depth on a tensor-core precision: d_out is [n][L], the cumulative
+                               outputs y_1 .. y_L of every point (every level of detail at once);
+                               not with gradients */
     uint8_t *d_exit_layers; /* optional device [n]: exit layer used per point (0xFF = NaN point) */
     void *d_workspace;      /* optional device scratch of >= sand_workspace_bytes() bytes, 256-byte aligned;
                                NULL = the model's own workspace (grown on demand; one stream at a time) */
@@ -212,6 +214,30 @@ size_t sand_trace_state_bytes(int64_t n_rays);
 sand_status sand_sphere_trace(sand_model m, const float *d_origin, int per_ray_origin, const float *d_dirs,
                               int64_t n_rays, const sand_trace_opts *topts, const sand_query_opts *qopts, float *d_t,
                               uint8_t *d_state, uint8_t *d_steps, float *d_grad, void *stream);
+
+/* ---------------------------------------------------------------- depth-map construction
+ * The volumetric network-depth map from the network itself (Sec. 3.2): for every leaf
+ * of the octree (desc, h_child as in sand_load_depth_map_mem) with h_near[node] != 0
+ * (the leaves whose cells meet the shape), Eq. 6 stores the maximum over k^3 sample
+ * points x of Eq. 5,
+ *   d(x) = min{ i : |y_L(x) - y_i(x)| < r  and  sign y_i(x) = sign y_L(x) },
+ * (sign(0) taken as +1; i = L always qualifies), y_i the cumulative outputs of Eq. 2
+ * evaluated on the tensor cores in opts->precision.  The samples are the cell-centred
+ * k x k x k lattice of the leaf, x = lo + (s + 1/2) side / k per axis (k a power of two,
+ * so every sample is exact in float32).  Far leaves get depth 0 (they answer with their
+ * stored value, Eq. 7), or with far_sign the sign-only case of Eq. 5, max-pooled.
+ * h_depth_out [n_nodes]: the leaves' depths, 0 for inner nodes.  Synchronous (the
+ * result is on the host on return); host arrays are the caller's.  The paper's
+ * r = 1.5e-4 assumes shapes normalised to the unit cube. */
+typedef struct {
+    int samples_per_axis;  /* k: 1, 2, 4, 8 or 16 */
+    float r;               /* > 0 */
+    int far_sign;          /* 0: far leaves keep depth 0; 1: sign-only case of Eq. 5 */
+    int precision;         /* a tensor-core sand_precision (SAND_FP32: float32 accuracy) */
+} sand_map_build_opts;
+sand_status sand_build_depth_map(sand_model m, const sand_depth_map_desc *desc, const int32_t *h_child,
+                                 const uint8_t *h_near, const sand_map_build_opts *opts, uint8_t *h_depth_out,
+                                 void *stream);
 
 /* Flags and counters a query leaves in its workspace (read after the query's
  * stream has been synchronised by this call). */

@@ -151,3 +151,72 @@ def query(model, octree, points, max_depth: int = 0, grad: bool = False, exit_la
 def full_depth(model, points, grad: bool = False):
     """The plain T-MLP evaluated to its last layer at every point (no depth map)."""
     return evaluate(model, points, model.n_layers, grad=grad)
+
+
+# ---------------------------------------------------------------------------------------------
+# Network-depth map from the network (Sec. 3.2, Eq. 5-7)
+# ---------------------------------------------------------------------------------------------
+def leaf_cells(child):
+    """Every leaf of a pointer octree over [-1, 1]^3 (root = node 0, the children of a node
+    consecutive in octant order ix | iy << 1 | iz << 2) as rows (node, level, ix, iy, iz):
+    the leaf's cell is [-1 + 2 ix / 2^level, -1 + 2 (ix + 1) / 2^level) per axis."""
+    child = np.asarray(child)
+    out = []
+    stack = [(0, 0, 0, 0, 0)]
+    while stack:
+        n, lv, ix, iy, iz = stack.pop()
+        c = int(child[n])
+        if c < 0:
+            out.append((n, lv, ix, iy, iz))
+            continue
+        for o in range(8):
+            stack.append((c + o, lv + 1, 2 * ix + (o & 1), 2 * iy + ((o >> 1) & 1), 2 * iz + ((o >> 2) & 1)))
+    return np.array(sorted(out), np.int64).reshape(-1, 5)
+
+
+def leaf_samples(cells, k: int):
+    """The k^3 cell-centred lattice of sample points in each leaf cell, float32 [n_leaves * k^3, 3]
+    (leaf-major, x fastest within a leaf): x = lo + (s + 1/2) side / k.  For a power-of-two k
+    every value is exact in float32."""
+    lv = cells[:, 1].astype(np.float64)
+    side = 2.0 / np.exp2(lv)
+    lo = -1.0 + cells[:, 2:5].astype(np.float64) * side[:, None]
+    s = np.arange(k, dtype=np.float64)
+    sz, sy, sx = np.meshgrid(s, s, s, indexing="ij")
+    sub = np.stack([sx.ravel(), sy.ravel(), sz.ravel()], axis=1)  # [k^3, 3], x fastest
+    pts = lo[:, None, :] + (sub[None, :, :] + 0.5) * (side / k)[:, None, None]
+    return pts.reshape(-1, 3).astype(np.float32)
+
+
+def required_depth(ys, r: float, near: bool = True):
+    """Eq. 5 per point from its cumulative outputs ys [n, L] (y_1 .. y_L): the smallest i with
+    sign(y_i) = sign(y_L) (sign(0) taken as +1), and, near the surface, |y_L - y_i| < r.
+    i = L always qualifies, so every point gets a depth in 1 .. L."""
+    ys = np.asarray(ys, np.float64)
+    yl = ys[:, -1:]
+    ok = np.where(ys >= 0, 1, -1) == np.where(yl >= 0, 1, -1)
+    if near:
+        ok &= np.abs(yl - ys) < r
+    return np.argmax(ok, axis=1).astype(np.int64) + 1
+
+
+def depth_map_from_network(model, child, near, k: int = 4, r: float = 1.5e-4, far_sign: bool = False):
+    """Eq. 6: the depth of a near leaf (near[node] != 0) is the maximum of Eq. 5 over its k^3
+    sample points; far leaves keep depth 0 (Eq. 7: they answer with their stored value), or,
+    with far_sign, get the maximum over their samples of the sign-only case of Eq. 5.
+    Returns (depth per node as uint8, sample points, their Eq. 5 depths, leaf row per sample,
+    the samples' y_1 .. y_L in float64)."""
+    near = np.asarray(near)
+    cells = leaf_cells(child)
+    use = np.array([bool(near[c[0]]) or far_sign for c in cells], bool)
+    cells = cells[use]
+    pts = leaf_samples(cells, k)
+    _, ys = evaluate(model, pts, model.n_layers, all_tails=True)
+    kk = k ** 3
+    leaf_row = np.repeat(np.arange(len(cells)), kk)
+    is_near = np.repeat(np.array([bool(near[c[0]]) for c in cells], bool), kk)
+    d = np.where(is_near, required_depth(ys, r, True), required_depth(ys, r, False))
+    depth = np.zeros(len(child), np.uint8)
+    for row, c in enumerate(cells):
+        depth[c[0]] = int(d[row * kk:(row + 1) * kk].max())
+    return depth, pts, d, leaf_row, ys

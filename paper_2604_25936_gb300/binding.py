@@ -45,7 +45,7 @@ class DepthMapDesc(ctypes.Structure):
 
 class QueryOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_depth", ctypes.c_int32), ("full_depth", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("d_exit_layers", ctypes.c_void_p), ("d_workspace", ctypes.c_void_p),
+                ("all_tails", ctypes.c_int32), ("d_exit_layers", ctypes.c_void_p), ("d_workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t), ("stage_events", ctypes.c_void_p)]
 
 
@@ -68,6 +68,11 @@ class TraceOpts(ctypes.Structure):
 RAY_MISS, RAY_HIT, RAY_STEPS, RAY_NAN = 0, 1, 2, 3
 
 
+class MapBuildOpts(ctypes.Structure):
+    _fields_ = [("samples_per_axis", ctypes.c_int32), ("r", ctypes.c_float), ("far_sign", ctypes.c_int32),
+                ("precision", ctypes.c_int32)]
+
+
 class QueryStats(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_uint32), ("n_network", ctypes.c_uint32), ("count", ctypes.c_uint32 * 16)]
 
@@ -77,7 +82,7 @@ EXPORTS = ("sand_load_tmlp", "sand_load_tmlp_mem", "sand_load_depth_map", "sand_
            "sand_workspace_bytes", "sand_query_sdf", "sand_query_sdf_grad", "sand_query_sdf_host",
            "sand_read_stats", "sand_model_desc", "sand_free", "sand_last_error", "sand_server_create",
            "sand_server_submit", "sand_server_wait", "sand_server_stats", "sand_server_destroy",
-           "sand_trace_state_bytes", "sand_sphere_trace")
+           "sand_trace_state_bytes", "sand_sphere_trace", "sand_build_depth_map")
 
 
 def lib() -> ctypes.CDLL:
@@ -112,6 +117,7 @@ def lib() -> ctypes.CDLL:
     L.sand_trace_state_bytes.restype = ctypes.c_size_t
     L.sand_sphere_trace.argtypes = [P, P, I32, P, I64, ctypes.POINTER(TraceOpts), ctypes.POINTER(QueryOpts), P, P, P,
                                     P, P]
+    L.sand_build_depth_map.argtypes = [P, ctypes.POINTER(DepthMapDesc), P, P, ctypes.POINTER(MapBuildOpts), P, P]
     for name in EXPORTS:
         if name not in ("sand_workspace_bytes", "sand_last_error", "sand_trace_state_bytes"):
             getattr(L, name).restype = ctypes.c_int
@@ -216,16 +222,19 @@ class Model:
 
     def query(self, points: torch.Tensor, precision: str = "fp32", max_depth: int = 0, full_depth: bool = False,
               exit_layers: bool = False, out: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None,
-              stream: Optional[torch.cuda.Stream] = None, events=None):
-        """SDF at every point (SAND inference; full_depth=True runs the plain T-MLP to layer L).
+              stream: Optional[torch.cuda.Stream] = None, events=None, all_tails: bool = False):
+        """SDF at every point (SAND inference; full_depth=True runs the plain T-MLP to layer L; with
+        all_tails as well, returns [n, L]: y_1 .. y_L of every point).
         events: optional three timing events recorded before the lookup, before and after the T-MLP kernel."""
         pts = _as_points(points, self.device)
         n = pts.shape[0]
         if out is None:
-            out = torch.empty(n, dtype=torch.float32, device=pts.device)
+            shape = (n, self.desc.n_layers) if all_tails else (n,)
+            out = torch.empty(shape, dtype=torch.float32, device=pts.device)
         el = torch.empty(n, dtype=torch.uint8, device=pts.device) if exit_layers else None
         ws = workspace if workspace is not None else self.workspace(0 if full_depth else n)
         o = self._opts(precision, max_depth, full_depth, el, ws, events)
+        o.all_tails = int(bool(all_tails))
         _check(lib().sand_query_sdf(self._h, ctypes.c_void_p(pts.data_ptr()), n, ctypes.c_void_p(out.data_ptr()),
                                     ctypes.byref(o), _stream_handle(stream)))
         return (out, el) if exit_layers else out
@@ -290,6 +299,25 @@ class Model:
                                        ctypes.c_void_p(steps.data_ptr()),
                                        ctypes.c_void_p(g.data_ptr() if g is not None else 0), _stream_handle(stream)))
         return t, state, steps, g
+
+    def build_depth_map(self, max_level: int, child: np.ndarray, near: np.ndarray, samples_per_axis: int = 4,
+                        r: float = 1.5e-4, far_sign: bool = False, precision: str = "fp32",
+                        stream: Optional[torch.cuda.Stream] = None) -> np.ndarray:
+        """Depths of the octree's leaves from this network (Eq. 5-6), uint8 per node; far leaves 0
+        unless far_sign.  `near` flags the leaves whose cells meet the shape."""
+        if precision not in PRECISION:
+            raise ValueError("precision must be one of %s" % sorted(PRECISION))
+        c = np.ascontiguousarray(child, np.int32)
+        nr = np.ascontiguousarray(near, np.uint8)
+        if c.size != nr.size:
+            raise ValueError("child and near must have one entry per node")
+        out = np.zeros(c.size, np.uint8)
+        desc = DepthMapDesc(int(max_level), int(self.desc.n_layers), c.size)
+        o = MapBuildOpts(int(samples_per_axis), float(r), int(bool(far_sign)), PRECISION[precision])
+        _check(lib().sand_build_depth_map(self._h, ctypes.byref(desc), c.ctypes.data_as(ctypes.c_void_p),
+                                          nr.ctypes.data_as(ctypes.c_void_p), ctypes.byref(o),
+                                          out.ctypes.data_as(ctypes.c_void_p), _stream_handle(stream)))
+        return out
 
     def stats(self, workspace: Optional[torch.Tensor] = None, stream: Optional[torch.cuda.Stream] = None) -> dict:
         """Flags and per-exit-layer counts left by the last query on `workspace` (synchronises the stream)."""

@@ -206,6 +206,7 @@ static sand_status model_precheck(sand_model m) {
 }
 
 int model_device(sand_model m) { return m->device; }
+int model_layers(sand_model m) { return m->desc.n_layers; }
 bool model_has_map(sand_model m) { return m->map_level >= 0; }
 bool model_precision_ready(sand_model m, int precision) {
     if (precision == SAND_FP32_SIMT) return true;
@@ -360,10 +361,15 @@ static sand_status run_query(sand_model m, const float *d_points, int64_t n, flo
     if ((reinterpret_cast<uintptr_t>(d_points) & 3) || (reinterpret_cast<uintptr_t>(d_out) & 3) ||
         (reinterpret_cast<uintptr_t>(d_grad) & 3)) { set_error("device buffers must be 4-byte aligned"); return SAND_EINVAL; }
     if (o.max_depth < 0) { set_error("max_depth < 0"); return SAND_EINVAL; }
+    if (o.all_tails && (!o.full_depth || d_grad)) {
+        set_error("all_tails needs full_depth and no gradient");
+        return SAND_EINVAL;
+    }
     if (!o.full_depth && m->map_level < 0) { set_error("no depth map loaded"); return SAND_ENOMAP; }
     if (o.full_depth && o.d_exit_layers) { set_error("exit layers are not produced in full-depth mode"); return SAND_EINVAL; }
     if (o.full_depth && d_count) { set_error("full-depth mode needs a host point count"); return SAND_EINVAL; }
     const bool simt = o.precision == SAND_FP32_SIMT || d_grad != nullptr;
+    if (o.all_tails && simt) { set_error("all_tails runs on the tensor-core precisions only"); return SAND_EUNSUPPORTED; }
     if (!simt && !tc_supported(m->desc, o.precision)) {
         set_error("precision %d is not supported for this model on the tensor-core path", o.precision);
         return SAND_EUNSUPPORTED;
@@ -398,7 +404,7 @@ static sand_status run_query(sand_model m, const float *d_points, int64_t n, flo
     } else {
         st = tc_prepare(&m->tc, m->desc, m->params.data(), o.precision);
         if (st) return st;
-        SAND_CUDA(launch_tmlp_tc(m->tc, m->simt, d_points, n, o.full_depth, ws, d_out, m->num_sms, s),
+        SAND_CUDA(launch_tmlp_tc(m->tc, m->simt, d_points, n, o.full_depth, ws, d_out, m->num_sms, s, o.all_tails),
                   "tensor-core T-MLP kernel");
     }
     if (ev) SAND_CUDA(cudaEventRecord(ev[2], s), "event record");
@@ -415,6 +421,26 @@ sand_status query_device_count(sand_model m, const float *d_points, int64_t n, c
         return SAND_EINVAL;
     }
     return run_query(m, d_points, n, d_out, d_grad, opts, s, d_count);
+}
+
+sand_status model_eval_all_tails(sand_model m, const float *d_pts, int64_t n, float *d_out, int precision,
+                                 cudaStream_t s) {
+    sand_status st = model_precheck(m);
+    if (st) return st;
+    if (n <= 0) return SAND_OK;
+    if (!tc_supported(m->desc, precision)) {
+        set_error("precision %d is not supported for this model on the tensor-core path", precision);
+        return SAND_EUNSUPPORTED;
+    }
+    void *ws = nullptr;
+    size_t wsb = 0;
+    st = ensure_workspace(m, 0, false, &ws, &wsb);
+    if (st) return st;
+    st = tc_prepare(&m->tc, m->desc, m->params.data(), precision);
+    if (st) return st;
+    SAND_CUDA(launch_init_header(ws, s), "workspace reset");
+    SAND_CUDA(launch_tmlp_tc(m->tc, m->simt, d_pts, n, 1, ws, d_out, m->num_sms, s, 1), "all-tails T-MLP kernel");
+    return SAND_OK;
 }
 
 sand_status model_trace_buffer(sand_model m, size_t bytes, void **out) {
@@ -465,7 +491,10 @@ sand_status sand_query_sdf_host(sand_model m, const float *h_points, int64_t n, 
     if (!h_points || !h_out || n < 0) { set_error("bad host buffers"); return SAND_EINVAL; }
     sand_query_opts o{};
     if (opts) o = *opts;
-    if (o.d_exit_layers) { set_error("d_exit_layers is not available for host queries"); return SAND_EINVAL; }
+    if (o.d_exit_layers || o.all_tails) {
+        set_error("d_exit_layers and all_tails are not available for host queries");
+        return SAND_EINVAL;
+    }
     DeviceGuard g(m->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t need = (size_t)n * 16;

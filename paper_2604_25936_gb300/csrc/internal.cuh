@@ -139,6 +139,10 @@ sand_status model_prepare(sand_model m, int precision);   // pack device weights
 // sized for n); opts->d_workspace must hold ws_layout(n).  Full-depth mode is not offered.
 sand_status query_device_count(sand_model m, const float *d_points, int64_t n, const uint32_t *d_count, float *d_out,
                                float *d_grad, const sand_query_opts *opts, cudaStream_t s);
+// y_1 .. y_L of n points (d_out [n][L]) on the tensor cores in `precision` (the model's workspace).
+sand_status model_eval_all_tails(sand_model m, const float *d_pts, int64_t n, float *d_out, int precision,
+                                 cudaStream_t s);
+int model_layers(sand_model m);
 // Grow-only device buffer owned by the model for the sphere tracer (stream-ordered reuse).
 sand_status model_trace_buffer(sand_model m, size_t bytes, void **out);
 

@@ -14,8 +14,9 @@ struct TcModel {
 
 bool tc_supported(const sand_tmlp_desc &d, int precision);
 sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params, int precision);
+// all_tails (with full_depth): out[i * L + l - 1] = y_l for every layer l of every point.
 cudaError_t launch_tmlp_tc(const TcModel &tc, const TmlpDev &M, const float *pts, int64_t n, int full_depth, void *ws,
-                           float *out, int num_sms, cudaStream_t s);
+                           float *out, int num_sms, cudaStream_t s, int all_tails = 0);
 void tc_release(TcModel *tc);
 
 }  // namespace sand

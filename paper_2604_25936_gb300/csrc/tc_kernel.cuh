@@ -85,6 +85,7 @@ struct TcParams {
     int first_mma;            // 1-based index of the first layer computed on the tensor cores (1)
     int l1_fold;              // layer 1 is one K = 16 fp16 MMA over split coordinates (not Fourier features)
     float x_scale;            // coordinates are scaled by this before the split
+    int all_tails;            // write y_1 .. y_L of every row (out[idx * L + l - 1]) instead of y at the exit layer
     int kpad;                 // padded K of the packed weight matrix (multiple of 64; of 128 in the FP8 mode)
     int n_stages;
     uint32_t stage_bytes;     // W * 128
@@ -772,7 +773,11 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                     float tl = t0v;
                     if (MULT && l >= 2) tl = t0v * (sb + __ldg(P.tb + 2 * (l - 1) + 1));
                     y += tl;
-                    if (d == l && idx >= 0) out[idx] = y;
+                    if (P.all_tails) {
+                        if (idx >= 0) out[idx * L + (l - 1)] = y;
+                    } else if (d == l && idx >= 0) {
+                        out[idx] = y;
+                    }
                 }
             }
         }
