@@ -401,6 +401,26 @@ def trace_bench(sand, model, tree, local: int, steps: int, precision: str = "fp3
     return res
 
 
+def map_build_bench(sand, model, local: int, steps: int):
+    """The network-depth map from the network (Eq. 5-7) for the level-7 scene octree: Eq. 5 on a
+    4^3 lattice per near leaf with r = 1.5e-4, max-pooled per leaf, float32 mode."""
+    import torch
+    tree = synth.scene_octree(7, N_LAYERS, far_field=True)
+    near = ((tree.child < 0) & (tree.depth > 0)).astype(np.uint8)
+    m = sand.Model.from_params(*model.header_ints(), model.omega0, model.flat(), device=local)
+    got = m.build_depth_map(tree.max_level, tree.child, near, samples_per_axis=4, r=1.5e-4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        got = m.build_depth_map(tree.max_level, tree.child, near, samples_per_axis=4, r=1.5e-4)
+    dt = (time.perf_counter() - t0) / steps
+    n_near = int(near.sum())
+    m.free()
+    return {"octree": "scene, level 7, far field", "near_leaves": n_near, "samples_per_leaf": 64,
+            "samples": n_near * 64, "r": 1.5e-4, "ms": dt * 1e3, "samples_per_s": n_near * 64 / dt,
+            "depth_histogram": np.bincount(got[near.astype(bool)], minlength=N_LAYERS + 1).tolist()}
+
+
 def run_profile_case(args):
     """The same model and map as the benchmark on a smaller point set, for ncu captures."""
     import torch
@@ -581,6 +601,10 @@ def main():
     if rank == 0 and not args.no_variants:
         tr = trace_bench(sand, model, synth.scene_octree(7, N_LAYERS, far_field=True), local, max(3, K // 4))
 
+    mapb = None
+    if rank == 0 and not args.no_variants:
+        mapb = map_build_bench(sand, model, local, max(2, K // 8))
+
     variant = None
     if rank == 0 and not args.no_variants:
         variant = precision_variant(sand, local, max(3, K // 4))
@@ -621,6 +645,7 @@ def main():
         "serve": serve,
         "precision_variant": variant,
         "sphere_trace": tr,
+        "depth_map_build": mapb,
         "serve_p99_ms": (serve or {}).get("bf16", {}).get("load_0.8", {}).get("p99_ms"),
     }
     if rank == 0:

@@ -182,6 +182,16 @@ sand_status sand_query_sdf_host(sand_model m, const float *h_points, int64_t n, 
 sand_status sand_query_sdf_noalloc(sand_model m, const float *d_points, int64_t n, float *d_out,
                                    const sand_query_opts *opts, void *stream);
 
+/* Octree-free dynamic exit (the ablation of Table 6): no depth map; every point runs
+ * layer by layer and stops at the first layer i whose tail |t_i| < r (the residual it
+ * adds, Eq. 2), returning y_i, or at layer L.  Rows stop individually; a 128-row tile of
+ * the tensor-core kernel stops issuing MMAs once all its rows have stopped (the points
+ * are not sorted, so stopped rows ride along until then).  d_out [n]; d_exit_layers
+ * [n] optional (the layer each point stopped at).  opts: only the precision (a
+ * tensor-core one) is taken; the model's own workspace is used. */
+sand_status sand_query_sdf_dynamic(sand_model m, const float *d_points, int64_t n, float r, float *d_out,
+                                   uint8_t *d_exit_layers, const sand_query_opts *opts, void *stream);
+
 /* ---------------------------------------------------------------- sphere tracing
  * Rendering use of the SAND SDF (Sec. 3.4 queries at ray samples; the paper
  * gives no tracing algorithm, this is classic sphere tracing).  Ray r has origin

@@ -220,3 +220,15 @@ def depth_map_from_network(model, child, near, k: int = 4, r: float = 1.5e-4, fa
     for row, c in enumerate(cells):
         depth[c[0]] = int(d[row * kk:(row + 1) * kk].max())
     return depth, pts, d, leaf_row, ys
+
+
+def dynamic_exit(model, points, r: float):
+    """The octree-free dynamic inference of Table 6: a point runs layer by layer and stops at
+    the first layer i whose tail |t_i| = |y_i - y_{i-1}| < r (y_0 = 0), or at layer L.
+    Returns (y at that layer, the layer as int64, all y_1 .. y_L in float64)."""
+    _, ys = evaluate(model, points, model.n_layers, all_tails=True)
+    t = np.diff(np.concatenate([np.zeros((ys.shape[0], 1)), ys], axis=1), axis=1)
+    stop = np.abs(t) < r
+    stop[:, -1] = True
+    d = np.argmax(stop, axis=1) + 1
+    return ys[np.arange(len(d)), d - 1], d.astype(np.int64), ys

@@ -82,7 +82,7 @@ EXPORTS = ("sand_load_tmlp", "sand_load_tmlp_mem", "sand_load_depth_map", "sand_
            "sand_workspace_bytes", "sand_query_sdf", "sand_query_sdf_grad", "sand_query_sdf_host",
            "sand_read_stats", "sand_model_desc", "sand_free", "sand_last_error", "sand_server_create",
            "sand_server_submit", "sand_server_wait", "sand_server_stats", "sand_server_destroy",
-           "sand_trace_state_bytes", "sand_sphere_trace", "sand_build_depth_map")
+           "sand_trace_state_bytes", "sand_sphere_trace", "sand_build_depth_map", "sand_query_sdf_dynamic")
 
 
 def lib() -> ctypes.CDLL:
@@ -118,6 +118,7 @@ def lib() -> ctypes.CDLL:
     L.sand_sphere_trace.argtypes = [P, P, I32, P, I64, ctypes.POINTER(TraceOpts), ctypes.POINTER(QueryOpts), P, P, P,
                                     P, P]
     L.sand_build_depth_map.argtypes = [P, ctypes.POINTER(DepthMapDesc), P, P, ctypes.POINTER(MapBuildOpts), P, P]
+    L.sand_query_sdf_dynamic.argtypes = [P, P, I64, ctypes.c_float, P, P, ctypes.POINTER(QueryOpts), P]
     for name in EXPORTS:
         if name not in ("sand_workspace_bytes", "sand_last_error", "sand_trace_state_bytes"):
             getattr(L, name).restype = ctypes.c_int
@@ -299,6 +300,20 @@ class Model:
                                        ctypes.c_void_p(steps.data_ptr()),
                                        ctypes.c_void_p(g.data_ptr() if g is not None else 0), _stream_handle(stream)))
         return t, state, steps, g
+
+    def query_dynamic(self, points: torch.Tensor, r: float = 1.5e-4, precision: str = "fp32",
+                      stream: Optional[torch.cuda.Stream] = None):
+        """Octree-free dynamic exit (Table 6): (y, exit layer uint8) per point, stopping at the first
+        layer whose tail |t_i| < r."""
+        pts = _as_points(points, self.device)
+        n = pts.shape[0]
+        out = torch.empty(n, dtype=torch.float32, device=pts.device)
+        el = torch.empty(n, dtype=torch.uint8, device=pts.device)
+        o = self._opts(precision, 0, False, None, None)
+        _check(lib().sand_query_sdf_dynamic(self._h, ctypes.c_void_p(pts.data_ptr()), n, float(r),
+                                            ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(el.data_ptr()),
+                                            ctypes.byref(o), _stream_handle(stream)))
+        return out, el
 
     def build_depth_map(self, max_level: int, child: np.ndarray, near: np.ndarray, samples_per_axis: int = 4,
                         r: float = 1.5e-4, far_sign: bool = False, precision: str = "fp32",

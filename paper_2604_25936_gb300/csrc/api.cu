@@ -469,6 +469,44 @@ sand_status sand_query_sdf(sand_model m, const float *d_points, int64_t n, float
     return run_query(m, d_points, n, d_out, nullptr, opts, stream);
 }
 
+sand_status sand_query_sdf_dynamic(sand_model m, const float *d_points, int64_t n, float r, float *d_out,
+                                   uint8_t *d_exit_layers, const sand_query_opts *opts, void *stream) {
+    g_err.clear();
+    sand_status st = model_precheck(m);
+    if (st) return st;
+    if (n < 0 || n > 0x7fffffffLL) { set_error("n = %lld outside 0..2^31-1", (long long)n); return SAND_EINVAL; }
+    if (n == 0) return SAND_OK;
+    if (!d_points || !d_out) { set_error("NULL points or output"); return SAND_EINVAL; }
+    if (!(r > 0.f)) { set_error("r must be positive"); return SAND_EINVAL; }
+    if ((reinterpret_cast<uintptr_t>(d_points) & 3) || (reinterpret_cast<uintptr_t>(d_out) & 3)) {
+        set_error("device buffers must be 4-byte aligned");
+        return SAND_EINVAL;
+    }
+    sand_query_opts o{};
+    if (opts) o = *opts;
+    if (o.full_depth || o.all_tails || o.d_exit_layers || o.max_depth || o.d_workspace || o.stage_events) {
+        set_error("dynamic queries take only the precision from the query options");
+        return SAND_EINVAL;
+    }
+    if (!tc_supported(m->desc, o.precision)) {
+        set_error("precision %d is not supported for this model on the tensor-core path", o.precision);
+        return SAND_EUNSUPPORTED;
+    }
+    DeviceGuard g(m->device);
+    if (!g.ok) { set_error("cannot select device %d", m->device); return SAND_ECUDA; }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void *ws = nullptr;
+    size_t wsb = 0;
+    st = ensure_workspace(m, 0, false, &ws, &wsb);
+    if (st) return st;
+    st = tc_prepare(&m->tc, m->desc, m->params.data(), o.precision);
+    if (st) return st;
+    SAND_CUDA(launch_init_header(ws, s), "workspace reset");
+    SAND_CUDA(launch_tmlp_tc(m->tc, m->simt, d_points, n, 1, ws, d_out, m->num_sms, s, 0, r, d_exit_layers),
+              "dynamic-exit T-MLP kernel");
+    return SAND_OK;
+}
+
 sand_status sand_query_sdf_grad(sand_model m, const float *d_points, int64_t n, float *d_out, float *d_grad,
                                 const sand_query_opts *opts, void *stream) {
     g_err.clear();

@@ -86,6 +86,9 @@ struct TcParams {
     int l1_fold;              // layer 1 is one K = 16 fp16 MMA over split coordinates (not Fourier features)
     float x_scale;            // coordinates are scaled by this before the split
     int all_tails;            // write y_1 .. y_L of every row (out[idx * L + l - 1]) instead of y at the exit layer
+    float dyn_r;              // > 0: octree-free dynamic exit (full depth): a row stops at the first layer whose
+                              // tail |t_l| < dyn_r; a tile stops issuing MMAs once all its rows have stopped
+    uint8_t *exit_out;        // dynamic exit: the layer each row stopped at (optional)
     int kpad;                 // padded K of the packed weight matrix (multiple of 64; of 128 in the FP8 mode)
     int n_stages;
     uint32_t stage_bytes;     // W * 128
@@ -154,6 +157,13 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+// Named barrier among n threads that also counts the threads whose pred is true.
+__device__ __forceinline__ int named_count(int id, int n, bool pred) {
+    int c;
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %3, 0;\n\tbar.red.popc.u32 %0, %1, %2, p;\n\t}"
+                 : "=r"(c) : "r"(id), "r"(n), "r"((unsigned)pred) : "memory");
+    return c;
+}
 
 // K-major operand in shared memory with 128-byte swizzle: rows of 128 bytes,
 // 8-row groups 1024 bytes apart (stride byte offset), descriptor version 1.
@@ -411,6 +421,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
     uint64_t *x_empty = x_full + 1; // ... and read by slice 0 (128 arrivals)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + kNumBars);
     volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    volatile int *skip = reinterpret_cast<volatile int *>(tmem_slot + 2);  // dynamic exit: the tile is done
     float *tailx = reinterpret_cast<float *>(tmem_slot + 4);  // [kSlices - 1][2 values][128 rows]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -430,6 +441,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
         mbar_init(smem_u32(x_full), (kSlices - 1) * 128);
         mbar_init(smem_u32(x_empty), 128);
         *abort = 0;
+        *skip = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -501,16 +513,21 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             const uint64_t bd_step = (uint64_t)(P.stage_bytes >> 4);  // descriptor units per stage
             uint32_t pa[kMaxKBlocks] = {0, 0, 0, 0, 0, 0};
             bool ok = true, any_layer = false;
+            bool drained_credit = false;  // dynamic exit: the last drained accumulator was not overwritten
+            const bool dyn = P.dyn_r > 0.f;
             for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
                 const int Dt = tile_depth(t);
-                for (int l = P.first_mma; l <= Dt && ok; ++l) {
+                bool tile_skip = false;
+                for (int l = P.first_mma; l <= Dt && ok && !tile_skip; ++l) {
                     const int K = l == 1 ? P.D : W;
                     const int kb_n = (K + UPS - 1) / UPS;
                     const int ks_n = (K + UPK - 1) / UPK;  // the last FP8 K-step may be half zero padding
                     int e_seen = -1;  // last 64-unit block of the A operand waited for in this layer
                     ok = mbar_wait(smem_u32(&full_bar[s]), ph, abort, hdr, 3, true);
                     if (!ok) break;
-                    if (any_layer) {  // the previous layer's accumulator has been read out
+                    if (any_layer && drained_credit) {
+                        drained_credit = false;
+                    } else if (any_layer) {  // the previous layer's accumulator has been read out
                         ok = mbar_wait(smem_u32(d_drained), pdr, abort, hdr, 8, true);
                         pdr ^= 1;
                         if (!ok) break;
@@ -537,6 +554,11 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                                     e_seen = e;
                                     if (!ok) break;
                                     tc_fence_after();
+                                    if (dyn && e == 0 && *skip) {  // every row of the tile has stopped
+                                        *skip = 0;
+                                        tile_skip = true;
+                                        break;
+                                    }
                                 }
                                 const int cnt = min(SEG, nks - g0);
                                 const uint32_t acol = (uint32_t)g * 8u;  // 16 fp16 or 32 e4m3 K-elements = 8 TMEM columns
@@ -567,9 +589,27 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                                     }
                                 }
                             }
+                            if (tile_skip) break;
                             if (ok) mma_commit(smem_u32(&empty_bar[s]));
                             if (++s == (uint32_t)P.n_stages) { s = 0; ph ^= 1; }
                         }
+                        if (tile_skip) break;
+                    }
+                    if (tile_skip) {
+                        // hand back every weight stage the producer loads for the rest of this tile:
+                        // the current one (waited for, unused) and those of layers l .. Dt still to come
+                        mbar_arrive(smem_u32(&empty_bar[s]));
+                        if (++s == (uint32_t)P.n_stages) { s = 0; ph ^= 1; }
+                        int rest = kb_n * parts_l - 1;
+                        for (int l2 = l + 1; l2 <= Dt; ++l2) rest += ((W + UPS - 1) / UPS) * PARTS;
+                        for (int k = 0; k < rest && ok; ++k) {
+                            ok = mbar_wait(smem_u32(&full_bar[s]), ph, abort, hdr, 9, true);
+                            if (!ok) break;
+                            mbar_arrive(smem_u32(&empty_bar[s]));
+                            if (++s == (uint32_t)P.n_stages) { s = 0; ph ^= 1; }
+                        }
+                        drained_credit = true;  // layer l's accumulator drain was waited for, and nothing wrote it since
+                        break;
                     }
                     if (ok) mma_commit(smem_u32(d_full));
                 }
@@ -698,6 +738,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             const int64_t idx = cur.idx;
             const float x0 = cur.x0, x1 = cur.x1, x2 = cur.x2;
             float y = 0.f;
+            bool alive = idx >= 0;  // dynamic exit: this row still runs
             // ---- the A operand of layer 1: split coordinates, or the Fourier features
             if (P.l1_fold) {
                 put_a1(cur);
@@ -727,6 +768,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                 if (!ok) break;
                 tc_fence_after();
                 const bool last = l == Dt;
+                const bool dyn = P.dyn_r > 0.f;
                 const float *cs = c_all + (size_t)(l - 1) * 3 * W;
                 const float c1 = P.c1[l - 1];
                 float sa = 0.f, sb = 0.f;
@@ -740,7 +782,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                             tmem_wait_ld();
                             epilogue16<MODE, ACT, TAIL>(cs, W, c1, v, c0, !last, a_hi_l, a_lo_l, sa, sb);
                         }
-                        if (!last) signal(&a_ready[kb], true);
+                        if (!last && !dyn) signal(&a_ready[kb], true);
                     }
                     signal(d_drained, false);
                 } else {
@@ -756,14 +798,14 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                     epilogue16<MODE, ACT, TAIL>(cs, W, c1, v[0] + 16, su0 + 16, !last, a_hi_l, a_lo_l, sa, sb);
                     tmem_wait_ld();
                     signal(d_drained, false);  // the next layer may overwrite the accumulator
-                    if (!last) signal(&a_ready[0], true);
+                    if (!last && !dyn) signal(&a_ready[0], true);
 #pragma unroll
                     for (int kb = 1; kb < 4; ++kb) {
                         if (kb < KB) {
                             epilogue16<MODE, ACT, TAIL>(cs, W, c1, v[kb], 64 * kb + su0, !last, a_hi_l, a_lo_l, sa, sb);
                             epilogue16<MODE, ACT, TAIL>(cs, W, c1, v[kb] + 16, 64 * kb + su0 + 16, !last, a_hi_l, a_lo_l,
                                                         sa, sb);
-                            if (!last) signal(&a_ready[kb], true);
+                            if (!last && !dyn) signal(&a_ready[kb], true);
                         }
                     }
                 }
@@ -773,10 +815,28 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                     float tl = t0v;
                     if (MULT && l >= 2) tl = t0v * (sb + __ldg(P.tb + 2 * (l - 1) + 1));
                     y += tl;
-                    if (P.all_tails) {
+                    if (dyn) {
+                        if (alive && (fabsf(tl) < P.dyn_r || last)) {  // the row stops here
+                            out[idx] = y;
+                            if (P.exit_out) P.exit_out[idx] = (uint8_t)l;
+                            alive = false;
+                        }
+                    } else if (P.all_tails) {
                         if (idx >= 0) out[idx * L + (l - 1)] = y;
                     } else if (d == l && idx >= 0) {
                         out[idx] = y;
+                    }
+                }
+                if (dyn && !last) {
+                    // the tile goes on while any of its rows does: release the next layer (its A
+                    // operand is in TMEM already), or tell the MMA thread to skip the tile's rest
+                    const int n_alive = named_count(1, kEpiThreads, slice == 0 && alive);
+                    if (n_alive > 0) {
+                        for (int kb = 0; kb < KB; ++kb) signal(&a_ready[kb], true);
+                    } else {
+                        if (threadIdx.x == 64) *skip = 1;
+                        signal(&a_ready[0], true);
+                        break;
                     }
                 }
             }

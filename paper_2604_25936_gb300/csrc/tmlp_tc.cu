@@ -258,12 +258,14 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
 }
 
 cudaError_t launch_tmlp_tc(const TcModel &tc, const TmlpDev &M, const float *pts, int64_t n, int full_depth, void *ws,
-                           float *out, int num_sms, cudaStream_t s, int all_tails) {
+                           float *out, int num_sms, cudaStream_t s, int all_tails, float dyn_r, uint8_t *exit_out) {
     (void)M;
     TcPack *pk = static_cast<TcPack *>(tc.host);
     if (!pk) return cudaErrorInvalidValue;
     TcParams P = pk->P;
     P.all_tails = all_tails && full_depth ? 1 : 0;
+    P.dyn_r = full_depth && !P.all_tails ? dyn_r : 0.f;
+    P.exit_out = P.dyn_r > 0.f ? exit_out : nullptr;
     WsLayout Lw = ws_layout(full_depth ? 0 : n);
     char *base = static_cast<char *>(ws);
     WsHeader *hdr = reinterpret_cast<WsHeader *>(base);

@@ -96,3 +96,17 @@ def test_depth_map_brute_force():
                         best = max(best, di)
             expect[node] = best
         np.testing.assert_array_equal(depth, expect)
+
+
+@pytest.mark.parametrize("p,R,r,expect_layer,expect_y", [
+    ((0.05, 0.5, 0.0), 0.6, 1e-2, 2, 0.05 ** 2 - 0.36),          # t = (-.36, .0025, .25, 0): stops at 2
+    ((0.5, 0.05, 0.5), 0.6, 1e-2, 3, 0.25 + 0.0025 - 0.36),      # t_3 = .0025
+    ((0.5, 0.5, 0.5), 0.6, 1e-2, 4, 0.75 - 0.36),                # no tail below r: layer L
+    ((0.5, 0.5, 0.5), 0.05, 1e-2, 1, -0.0025),                   # |t_1| = R^2 = .0025 < r: layer 1
+])
+def test_dynamic_exit_closed_form(p, R, r, expect_layer, expect_y):
+    """Table 6's dynamic exit on the hand-built model, whose tails are -R^2, x^2, y^2, z^2."""
+    model = synth.relu_sphere_tmlp(R, width=8)
+    y, d, _ = oracle.dynamic_exit(model, np.array([p], np.float32), r)
+    assert d[0] == expect_layer
+    assert abs(y[0] - expect_y) < 1e-6
