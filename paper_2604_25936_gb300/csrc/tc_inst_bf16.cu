@@ -1,30 +1,4 @@
-// Instantiations of the tensor-core T-MLP kernel for the bf16 mode.
-#include "tc_kernel.cuh"
-
-namespace sand {
-
-template <int ACT, int TAIL>
-static cudaError_t launch_one(const CUtensorMap &map, const TcParams &P, const float *pts, const float4 *sorted,
-                              WsHeader *hdr, int64_t n, int full_depth, float *out, int grid, size_t smem,
-                              cudaStream_t s) {
-    auto kern = tmlp_tc_kernel<TC_BF16, ACT, TAIL>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<grid, kTcThreads, smem, s>>>(map, P, pts, sorted, hdr, n, full_depth, out);
-    return cudaGetLastError();
-}
-
-template <>
-cudaError_t launch_tc_mode<TC_BF16>(const CUtensorMap &map, const TcParams &P, int act, int tail, const float *pts,
-                                   const float4 *sorted, WsHeader *hdr, int64_t n, int full_depth, float *out,
-                                   int grid, size_t smem, cudaStream_t s) {
-    if (act == SAND_ACT_RELU)
-        return tail == SAND_TAIL_MULT
-                   ? launch_one<SAND_ACT_RELU, SAND_TAIL_MULT>(map, P, pts, sorted, hdr, n, full_depth, out, grid, smem, s)
-                   : launch_one<SAND_ACT_RELU, SAND_TAIL_LINEAR>(map, P, pts, sorted, hdr, n, full_depth, out, grid, smem, s);
-    return tail == SAND_TAIL_MULT
-               ? launch_one<SAND_ACT_SINE, SAND_TAIL_MULT>(map, P, pts, sorted, hdr, n, full_depth, out, grid, smem, s)
-               : launch_one<SAND_ACT_SINE, SAND_TAIL_LINEAR>(map, P, pts, sorted, hdr, n, full_depth, out, grid, smem, s);
-}
-
-}  // namespace sand
+// Tensor-core T-MLP kernel instantiations: the bf16 mode.
+#define SAND_INST_MODE TC_BF16
+#define SAND_INST_EXT false
+#include "tc_inst_body.cuh"

@@ -395,7 +395,7 @@ __device__ __forceinline__ void epilogue16(const float *cs, int W, float c1, con
     }
 }
 
-template <int MODE, int ACT, int TAIL>
+template <int MODE, int ACT, int TAIL, bool EXT>
 __global__ void __launch_bounds__(kTcThreads, 1)
 tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const float *__restrict__ pts,
                const float4 *__restrict__ sorted, WsHeader *hdr, int64_t n, int full_depth, float *__restrict__ out) {
@@ -514,7 +514,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             uint32_t pa[kMaxKBlocks] = {0, 0, 0, 0, 0, 0};
             bool ok = true, any_layer = false;
             bool drained_credit = false;  // dynamic exit: the last drained accumulator was not overwritten
-            const bool dyn = P.dyn_r > 0.f;
+            const bool dyn = EXT && P.dyn_r > 0.f;
             for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
                 const int Dt = tile_depth(t);
                 bool tile_skip = false;
@@ -768,7 +768,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                 if (!ok) break;
                 tc_fence_after();
                 const bool last = l == Dt;
-                const bool dyn = P.dyn_r > 0.f;
+                const bool dyn = EXT && P.dyn_r > 0.f;
                 const float *cs = c_all + (size_t)(l - 1) * 3 * W;
                 const float c1 = P.c1[l - 1];
                 float sa = 0.f, sb = 0.f;
@@ -821,7 +821,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                             if (P.exit_out) P.exit_out[idx] = (uint8_t)l;
                             alive = false;
                         }
-                    } else if (P.all_tails) {
+                    } else if (EXT && P.all_tails) {
                         if (idx >= 0) out[idx * L + (l - 1)] = y;
                     } else if (d == l && idx >= 0) {
                         out[idx] = y;
@@ -850,8 +850,10 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
     }
 }
 
-// Launch one instantiation (defined in the per-mode translation units).
-template <int MODE>
+// Launch one instantiation (defined in the per-mode translation units).  EXT: the extended
+// outputs (all tails, dynamic exit) are compiled in; the plain query path carries none of
+// their code, which its single MMA-issuing thread would otherwise pay for at every layer.
+template <int MODE, bool EXT>
 cudaError_t launch_tc_mode(const CUtensorMap &map, const TcParams &P, int act, int tail, const float *pts,
                            const float4 *sorted, WsHeader *hdr, int64_t n, int full_depth, float *out, int grid,
                            size_t smem, cudaStream_t s);

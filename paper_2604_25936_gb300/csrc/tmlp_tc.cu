@@ -275,20 +275,17 @@ cudaError_t launch_tmlp_tc(const TcModel &tc, const TmlpDev &M, const float *pts
     const int64_t tiles = (n + kTileM - 1) / kTileM;
     int grid = num_sms;
     if (tiles < grid) grid = (int)(tiles > 0 ? tiles : 1);
+    const bool ext = P.all_tails || P.dyn_r > 0.f;
+#define SAND_LAUNCH(M)                                                                                              \
+    (ext ? launch_tc_mode<M, true>(pk->map, P, P.act, P.tail_kind, pts, sorted, hdr, n, full_depth, out, grid, smem, s) \
+         : launch_tc_mode<M, false>(pk->map, P, P.act, P.tail_kind, pts, sorted, hdr, n, full_depth, out, grid, smem, s))
     switch (pk->mode) {
-        case TC_SPLIT16:
-            return launch_tc_mode<TC_SPLIT16>(pk->map, P, P.act, P.tail_kind, pts, sorted, hdr, n, full_depth, out, grid,
-                                              smem, s);
-        case TC_F16:
-            return launch_tc_mode<TC_F16>(pk->map, P, P.act, P.tail_kind, pts, sorted, hdr, n, full_depth, out, grid, smem,
-                                          s);
-        case TC_FP8:
-            return launch_tc_mode<TC_FP8>(pk->map, P, P.act, P.tail_kind, pts, sorted, hdr, n, full_depth, out, grid, smem,
-                                          s);
-        default:
-            return launch_tc_mode<TC_BF16>(pk->map, P, P.act, P.tail_kind, pts, sorted, hdr, n, full_depth, out, grid, smem,
-                                           s);
+        case TC_SPLIT16: return SAND_LAUNCH(TC_SPLIT16);
+        case TC_F16: return SAND_LAUNCH(TC_F16);
+        case TC_FP8: return SAND_LAUNCH(TC_FP8);
+        default: return SAND_LAUNCH(TC_BF16);
     }
+#undef SAND_LAUNCH
 }
 
 void tc_release(TcModel *tc) {
