@@ -421,6 +421,30 @@ def map_build_bench(sand, model, local: int, steps: int):
             "depth_histogram": np.bincount(got[near.astype(bool)], minlength=N_LAYERS + 1).tolist()}
 
 
+def dynamic_bench(sand, model, x, n: int, local: int, steps: int):
+    """The octree-free dynamic exit of Table 6 on the benchmark lattice (no depth map), at the
+    paper's r = 1.5e-4 and at r = 0.05, float32 mode."""
+    import torch
+    m = sand.Model.from_params(*model.header_ints(), model.omega0, model.flat(), device=local)
+    stream = torch.cuda.current_stream()
+    res = {"lattice_points": n, "note": "rows stop at the first tail |t_i| < r; a 128-row tile stops when all its rows have"}
+    for r in (1.5e-4, 0.05):
+        for _ in range(2):
+            y, el = m.query_dynamic(x, r=r)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps):
+            y, el = m.query_dynamic(x, r=r)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / steps
+        res["r=%g" % r] = {"ms": ms, "queries_per_s": n / (ms / 1e3),
+                           "exit_layer_histogram": torch.bincount(el.long(), minlength=N_LAYERS + 1).tolist()}
+    m.free()
+    return res
+
+
 def run_profile_case(args):
     """The same model and map as the benchmark on a smaller point set, for ncu captures."""
     import torch
@@ -601,6 +625,10 @@ def main():
     if rank == 0 and not args.no_variants:
         tr = trace_bench(sand, model, synth.scene_octree(7, N_LAYERS, far_field=True), local, max(3, K // 4))
 
+    dynb = None
+    if rank == 0 and not args.no_variants:
+        dynb = dynamic_bench(sand, model, x, n, local, max(2, K // 8))
+
     mapb = None
     if rank == 0 and not args.no_variants:
         mapb = map_build_bench(sand, model, local, max(2, K // 8))
@@ -646,6 +674,7 @@ def main():
         "precision_variant": variant,
         "sphere_trace": tr,
         "depth_map_build": mapb,
+        "dynamic_exit": dynb,
         "serve_p99_ms": (serve or {}).get("bf16", {}).get("load_0.8", {}).get("p99_ms"),
     }
     if rank == 0:
