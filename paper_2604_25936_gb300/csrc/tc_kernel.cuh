@@ -91,7 +91,7 @@ struct TcParams {
     uint8_t *exit_out;        // dynamic exit: the layer each row stopped at (optional)
     int kpad;                 // padded K of the packed weight matrix (multiple of 64; of 128 in the FP8 mode)
     int n_stages;
-    uint32_t stage_bytes;     // W * 128
+    uint32_t stage_bytes;     // parts x W x 128: one K-block of the weights (hi and lo in the float32 mode)
     uint32_t tmem_cols;       // power of two >= W + parts * W / 2
     int box_rows;             // rows per TMA box: W, or W / 2 when W > 256 (box dimensions are at most 256)
     int n_split;              // first MMA column group when W > 256 (a multiple of 16)
@@ -469,17 +469,19 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                 for (int l = P.first_mma; l <= Dt && ok; ++l) {
                     const int kb_n = ((l == 1 ? P.D : W) + UPS - 1) / UPS;
                     const int parts_l = (l == 1 && P.l1_fold) ? 1 : PARTS;  // the folded layer 1 has one block
-                    for (int kb = 0; kb < kb_n && ok; ++kb)
-                        for (int p = 0; p < parts_l && ok; ++p, ++it) {
-                            const uint32_t s = it % P.n_stages, ph = (it / P.n_stages) & 1;
-                            ok = mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1, abort, hdr, 1, true);
-                            if (!ok) break;
-                            mbar_arrive_tx(smem_u32(&full_bar[s]), P.stage_bytes);
+                    // one stage per K-block: the float32 mode's hi and lo weights side by side
+                    for (int kb = 0; kb < kb_n && ok; ++kb, ++it) {
+                        const uint32_t s = it % P.n_stages, ph = (it / P.n_stages) & 1;
+                        ok = mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1, abort, hdr, 1, true);
+                        if (!ok) break;
+                        mbar_arrive_tx(smem_u32(&full_bar[s]), (uint32_t)parts_l * (uint32_t)W * 128u);
+                        for (int p = 0; p < parts_l; ++p) {
                             const int row0 = ((l - P.first_mma) * PARTS + p) * W;
                             for (int bx = 0; bx < W; bx += P.box_rows)  // one box of W rows, or two of W/2
-                                tma_load_2d(smem_u32(stage_base + (size_t)s * P.stage_bytes + (size_t)bx * 128), &wmap,
-                                            smem_u32(&full_bar[s]), kb * UPS, row0 + bx);
+                                tma_load_2d(smem_u32(stage_base + (size_t)s * P.stage_bytes + (size_t)(p * W + bx) * 128),
+                                            &wmap, smem_u32(&full_bar[s]), kb * UPS, row0 + bx);
                         }
+                    }
                 }
             }
             if (!ok) {  // drain copies still in flight before the CTA can exit
@@ -534,74 +536,76 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                     }
                     any_layer = true;
                     const bool fold = l == 1 && P.l1_fold;
-                    const int parts_l = fold ? 1 : PARTS;
                     for (int kb = 0; kb < kb_n && ok; ++kb) {
-                        for (int p = 0; p < parts_l && ok; ++p) {
-                            if (kb + p > 0) ok = mbar_wait(smem_u32(&full_bar[s]), ph, abort, hdr, 3, true);
-                            if (!ok) break;
-                            tc_fence_after();
-                            const uint64_t bd = bd_base + (uint64_t)s * bd_step;
-                            const int nks = min(4, ks_n - kb * 4);  // K-steps of this stage holding real units
-                            // runs of K-steps that read one 64-unit block of the A operand: the whole
-                            // stage (16-bit operands), or halves of it (FP8: 128 units per stage)
-                            constexpr int SEG = MODE == TC_FP8 ? 2 : 4;
-                            for (int g0 = 0; g0 < nks && ok; g0 += SEG) {
-                                const int g = kb * 4 + g0;
-                                const int e = (g * UPK) >> 6;  // block of the A operand these K-steps read
-                                if (e > e_seen) {
-                                    ok = mbar_wait(smem_u32(&a_ready[e]), pa[e], abort, hdr, 2, true);
-                                    pa[e] ^= 1;
-                                    e_seen = e;
-                                    if (!ok) break;
-                                    tc_fence_after();
-                                    if (dyn && e == 0 && *skip) {  // every row of the tile has stopped
-                                        *skip = 0;
-                                        tile_skip = true;
-                                        break;
-                                    }
+                        if (kb > 0) ok = mbar_wait(smem_u32(&full_bar[s]), ph, abort, hdr, 3, true);
+                        if (!ok) break;
+                        tc_fence_after();
+                        const uint64_t bd = bd_base + (uint64_t)s * bd_step;
+                        const uint64_t bd_lo = bd + (uint64_t)W * 8u;  // the lo weights follow the hi rows
+                        const int nks = min(4, ks_n - kb * 4);  // K-steps of this stage holding real units
+                        // runs of K-steps that read one 64-unit block of the A operand: the whole
+                        // stage (16-bit operands), or halves of it (FP8: 128 units per stage)
+                        constexpr int SEG = MODE == TC_FP8 ? 2 : 4;
+                        for (int g0 = 0; g0 < nks && ok; g0 += SEG) {
+                            const int g = kb * 4 + g0;
+                            const int e = (g * UPK) >> 6;  // block of the A operand these K-steps read
+                            if (e > e_seen) {
+                                ok = mbar_wait(smem_u32(&a_ready[e]), pa[e], abort, hdr, 2, true);
+                                pa[e] ^= 1;
+                                e_seen = e;
+                                if (!ok) break;
+                                tc_fence_after();
+                                if (dyn && e == 0 && *skip) {  // every row of the tile has stopped
+                                    *skip = 0;
+                                    tile_skip = true;
+                                    break;
                                 }
-                                const int cnt = min(SEG, nks - g0);
-                                const uint32_t acol = (uint32_t)g * 8u;  // 16 fp16 or 32 e4m3 K-elements = 8 TMEM columns
-                                const uint32_t acc = (p != 0 || g != 0) ? 1u : 0u;
-                                const uint32_t a_op = a_hi + acol;
-                                if (fold) {  // layer 1: one fp16 K-step per column group, whatever the mode
-                                    mma_ts<TC_F16>(tmem, a_op, bd, idesc0_l1, 0u);
-                                    if (n1 > 0) mma_ts<TC_F16>(tmem + (uint32_t)n0, a_op, bd + (uint64_t)n0 * 8u, idesc1_l1, 0u);
-                                    continue;
-                                }
-                                for (int grp = 0; grp < (n1 > 0 ? 2 : 1); ++grp) {
-                                    // column group grp: accumulator columns and B rows from n0 on for grp 1
-                                    const uint32_t dcol = grp ? tmem + (uint32_t)n0 : tmem;
-                                    const uint32_t id = grp ? idesc1 : idesc0;
-                                    const uint64_t bk = bd + (uint64_t)(2 * g0) + (grp ? (uint64_t)n0 * 8u : 0u);
-                                    if (PARTS == 2 && p == 0 && cnt == 4) {
-                                        mma_k4x2(dcol, a_op, a_lo + acol, bk, id, acc);
-                                    } else if (cnt == 4) {
-                                        mma_k4<MODE>(dcol, a_op, bk, id, acc);
-                                    } else if (cnt == 2 && PARTS == 1) {
-                                        mma_k2<MODE>(dcol, a_op, bk, id, acc);
-                                    } else {  // a ragged last stage: one K-step at a time
-                                        for (int k = 0; k < cnt; ++k) {
-                                            const uint32_t ak = k == 0 ? acc : 1u;
-                                            mma_ts<MODE>(dcol, a_op + 8u * k, bk + 2u * k, id, ak);
-                                            if (PARTS == 2 && p == 0) mma_ts<MODE>(dcol, a_lo + acol + 8u * k, bk + 2u * k, id, 1u);
+                            }
+                            const int cnt = min(SEG, nks - g0);
+                            const uint32_t acol = (uint32_t)g * 8u;  // 16 fp16 or 32 e4m3 K-elements = 8 TMEM columns
+                            const uint32_t acc = g != 0 ? 1u : 0u;
+                            const uint32_t a_op = a_hi + acol;
+                            if (fold) {  // layer 1: one fp16 K-step per column group, whatever the mode
+                                mma_ts<TC_F16>(tmem, a_op, bd, idesc0_l1, 0u);
+                                if (n1 > 0) mma_ts<TC_F16>(tmem + (uint32_t)n0, a_op, bd + (uint64_t)n0 * 8u, idesc1_l1, 0u);
+                                continue;
+                            }
+                            for (int grp = 0; grp < (n1 > 0 ? 2 : 1); ++grp) {
+                                // column group grp: accumulator columns and B rows from n0 on for grp 1
+                                const uint32_t dcol = grp ? tmem + (uint32_t)n0 : tmem;
+                                const uint32_t id = grp ? idesc1 : idesc0;
+                                const uint64_t goff = (uint64_t)(2 * g0) + (grp ? (uint64_t)n0 * 8u : 0u);
+                                const uint64_t bk = bd + goff;
+                                if (PARTS == 2 && cnt == 4) {
+                                    mma_k4x2(dcol, a_op, a_lo + acol, bk, id, acc);   // A_hi B_hi + A_lo B_hi
+                                    mma_k4<MODE>(dcol, a_op, bd_lo + goff, id, 1u);  // A_hi B_lo
+                                } else if (cnt == 4) {
+                                    mma_k4<MODE>(dcol, a_op, bk, id, acc);
+                                } else if (cnt == 2 && PARTS == 1) {
+                                    mma_k2<MODE>(dcol, a_op, bk, id, acc);
+                                } else {  // a ragged last stage: one K-step at a time
+                                    for (int k = 0; k < cnt; ++k) {
+                                        const uint32_t ak = k == 0 ? acc : 1u;
+                                        mma_ts<MODE>(dcol, a_op + 8u * k, bk + 2u * k, id, ak);
+                                        if (PARTS == 2) {
+                                            mma_ts<MODE>(dcol, a_lo + acol + 8u * k, bk + 2u * k, id, 1u);
+                                            mma_ts<MODE>(dcol, a_op + 8u * k, bd_lo + goff + 2u * k, id, 1u);
                                         }
                                     }
                                 }
                             }
-                            if (tile_skip) break;
-                            if (ok) mma_commit(smem_u32(&empty_bar[s]));
-                            if (++s == (uint32_t)P.n_stages) { s = 0; ph ^= 1; }
                         }
                         if (tile_skip) break;
+                        if (ok) mma_commit(smem_u32(&empty_bar[s]));
+                        if (++s == (uint32_t)P.n_stages) { s = 0; ph ^= 1; }
                     }
                     if (tile_skip) {
                         // hand back every weight stage the producer loads for the rest of this tile:
                         // the current one (waited for, unused) and those of layers l .. Dt still to come
                         mbar_arrive(smem_u32(&empty_bar[s]));
                         if (++s == (uint32_t)P.n_stages) { s = 0; ph ^= 1; }
-                        int rest = kb_n * parts_l - 1;
-                        for (int l2 = l + 1; l2 <= Dt; ++l2) rest += ((W + UPS - 1) / UPS) * PARTS;
+                        int rest = kb_n - 1;
+                        for (int l2 = l + 1; l2 <= Dt; ++l2) rest += (W + UPS - 1) / UPS;
                         for (int k = 0; k < rest && ok; ++k) {
                             ok = mbar_wait(smem_u32(&full_bar[s]), ph, abort, hdr, 9, true);
                             if (!ok) break;
