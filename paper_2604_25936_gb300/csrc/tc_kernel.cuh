@@ -403,6 +403,9 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
     constexpr bool MULT = TAIL == SAND_TAIL_MULT;
     constexpr int UPS = MODE == TC_FP8 ? 128 : 64;  // K-units per weight stage (one 128-byte row per unit)
     constexpr int UPK = MODE == TC_FP8 ? 32 : 16;   // K-units per MMA (32 bytes of every row)
+    // A stage holds two W x 128-byte sub-blocks: the hi and lo weights of one K-block (float32
+    // mode), or two consecutive K-blocks (one-part modes)
+    constexpr int KBS = PARTS == 2 ? 1 : 2;         // K-blocks per stage
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int W = P.W, L = P.L;
@@ -469,16 +472,20 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                 for (int l = P.first_mma; l <= Dt && ok; ++l) {
                     const int kb_n = ((l == 1 ? P.D : W) + UPS - 1) / UPS;
                     const int parts_l = (l == 1 && P.l1_fold) ? 1 : PARTS;  // the folded layer 1 has one block
-                    // one stage per K-block: the float32 mode's hi and lo weights side by side
-                    for (int kb = 0; kb < kb_n && ok; ++kb, ++it) {
+                    const int sb_n = (kb_n + KBS - 1) / KBS;
+                    for (int sb = 0; sb < sb_n && ok; ++sb, ++it) {
                         const uint32_t s = it % P.n_stages, ph = (it / P.n_stages) & 1;
                         ok = mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1, abort, hdr, 1, true);
                         if (!ok) break;
-                        mbar_arrive_tx(smem_u32(&full_bar[s]), (uint32_t)parts_l * (uint32_t)W * 128u);
-                        for (int p = 0; p < parts_l; ++p) {
+                        // sub-block j: part j of K-block sb (float32 mode), or K-block KBS sb + j
+                        const int subs = PARTS == 2 ? parts_l : min(KBS, kb_n - sb * KBS);
+                        mbar_arrive_tx(smem_u32(&full_bar[s]), (uint32_t)subs * (uint32_t)W * 128u);
+                        for (int j = 0; j < subs; ++j) {
+                            const int p = PARTS == 2 ? j : 0;
+                            const int kb = PARTS == 2 ? sb : sb * KBS + j;
                             const int row0 = ((l - P.first_mma) * PARTS + p) * W;
                             for (int bx = 0; bx < W; bx += P.box_rows)  // one box of W rows, or two of W/2
-                                tma_load_2d(smem_u32(stage_base + (size_t)s * P.stage_bytes + (size_t)(p * W + bx) * 128),
+                                tma_load_2d(smem_u32(stage_base + (size_t)s * P.stage_bytes + (size_t)(j * W + bx) * 128),
                                             &wmap, smem_u32(&full_bar[s]), kb * UPS, row0 + bx);
                         }
                     }
@@ -536,60 +543,66 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                     }
                     any_layer = true;
                     const bool fold = l == 1 && P.l1_fold;
-                    for (int kb = 0; kb < kb_n && ok; ++kb) {
-                        if (kb > 0) ok = mbar_wait(smem_u32(&full_bar[s]), ph, abort, hdr, 3, true);
+                    const int sb_n = (kb_n + KBS - 1) / KBS;
+                    for (int sb = 0; sb < sb_n && ok; ++sb) {
+                        if (sb > 0) ok = mbar_wait(smem_u32(&full_bar[s]), ph, abort, hdr, 3, true);
                         if (!ok) break;
                         tc_fence_after();
-                        const uint64_t bd = bd_base + (uint64_t)s * bd_step;
-                        const uint64_t bd_lo = bd + (uint64_t)W * 8u;  // the lo weights follow the hi rows
-                        const int nks = min(4, ks_n - kb * 4);  // K-steps of this stage holding real units
-                        // runs of K-steps that read one 64-unit block of the A operand: the whole
-                        // stage (16-bit operands), or halves of it (FP8: 128 units per stage)
-                        constexpr int SEG = MODE == TC_FP8 ? 2 : 4;
-                        for (int g0 = 0; g0 < nks && ok; g0 += SEG) {
-                            const int g = kb * 4 + g0;
-                            const int e = (g * UPK) >> 6;  // block of the A operand these K-steps read
-                            if (e > e_seen) {
-                                ok = mbar_wait(smem_u32(&a_ready[e]), pa[e], abort, hdr, 2, true);
-                                pa[e] ^= 1;
-                                e_seen = e;
-                                if (!ok) break;
-                                tc_fence_after();
-                                if (dyn && e == 0 && *skip) {  // every row of the tile has stopped
-                                    *skip = 0;
-                                    tile_skip = true;
-                                    break;
+                        const uint64_t bd_stage = bd_base + (uint64_t)s * bd_step;
+                        for (int jb = 0; jb < KBS && ok && !tile_skip; ++jb) {
+                            const int kb = sb * KBS + jb;
+                            if (kb >= kb_n) break;
+                            const uint64_t bd = bd_stage + (uint64_t)(jb * W) * 8u;  // this K-block's sub-block
+                            const uint64_t bd_lo = bd_stage + (uint64_t)W * 8u;  // float32 mode: the lo weights
+                            const int nks = min(4, ks_n - kb * 4);  // K-steps of this stage holding real units
+                            // runs of K-steps that read one 64-unit block of the A operand: the whole
+                            // stage (16-bit operands), or halves of it (FP8: 128 units per stage)
+                            constexpr int SEG = MODE == TC_FP8 ? 2 : 4;
+                            for (int g0 = 0; g0 < nks && ok; g0 += SEG) {
+                                const int g = kb * 4 + g0;
+                                const int e = (g * UPK) >> 6;  // block of the A operand these K-steps read
+                                if (e > e_seen) {
+                                    ok = mbar_wait(smem_u32(&a_ready[e]), pa[e], abort, hdr, 2, true);
+                                    pa[e] ^= 1;
+                                    e_seen = e;
+                                    if (!ok) break;
+                                    tc_fence_after();
+                                    if (dyn && e == 0 && *skip) {  // every row of the tile has stopped
+                                        *skip = 0;
+                                        tile_skip = true;
+                                        break;
+                                    }
                                 }
-                            }
-                            const int cnt = min(SEG, nks - g0);
-                            const uint32_t acol = (uint32_t)g * 8u;  // 16 fp16 or 32 e4m3 K-elements = 8 TMEM columns
-                            const uint32_t acc = g != 0 ? 1u : 0u;
-                            const uint32_t a_op = a_hi + acol;
-                            if (fold) {  // layer 1: one fp16 K-step per column group, whatever the mode
-                                mma_ts<TC_F16>(tmem, a_op, bd, idesc0_l1, 0u);
-                                if (n1 > 0) mma_ts<TC_F16>(tmem + (uint32_t)n0, a_op, bd + (uint64_t)n0 * 8u, idesc1_l1, 0u);
-                                continue;
-                            }
-                            for (int grp = 0; grp < (n1 > 0 ? 2 : 1); ++grp) {
-                                // column group grp: accumulator columns and B rows from n0 on for grp 1
-                                const uint32_t dcol = grp ? tmem + (uint32_t)n0 : tmem;
-                                const uint32_t id = grp ? idesc1 : idesc0;
-                                const uint64_t goff = (uint64_t)(2 * g0) + (grp ? (uint64_t)n0 * 8u : 0u);
-                                const uint64_t bk = bd + goff;
-                                if (PARTS == 2 && cnt == 4) {
-                                    mma_k4x2(dcol, a_op, a_lo + acol, bk, id, acc);   // A_hi B_hi + A_lo B_hi
-                                    mma_k4<MODE>(dcol, a_op, bd_lo + goff, id, 1u);  // A_hi B_lo
-                                } else if (cnt == 4) {
-                                    mma_k4<MODE>(dcol, a_op, bk, id, acc);
-                                } else if (cnt == 2 && PARTS == 1) {
-                                    mma_k2<MODE>(dcol, a_op, bk, id, acc);
-                                } else {  // a ragged last stage: one K-step at a time
-                                    for (int k = 0; k < cnt; ++k) {
-                                        const uint32_t ak = k == 0 ? acc : 1u;
-                                        mma_ts<MODE>(dcol, a_op + 8u * k, bk + 2u * k, id, ak);
-                                        if (PARTS == 2) {
-                                            mma_ts<MODE>(dcol, a_lo + acol + 8u * k, bk + 2u * k, id, 1u);
-                                            mma_ts<MODE>(dcol, a_op + 8u * k, bd_lo + goff + 2u * k, id, 1u);
+                                const int cnt = min(SEG, nks - g0);
+                                const uint32_t acol = (uint32_t)g * 8u;  // 16 fp16 or 32 e4m3 K-elements = 8 TMEM columns
+                                const uint32_t acc = g != 0 ? 1u : 0u;
+                                const uint32_t a_op = a_hi + acol;
+                                if (fold) {  // layer 1: one fp16 K-step per column group, whatever the mode
+                                    mma_ts<TC_F16>(tmem, a_op, bd, idesc0_l1, 0u);
+                                    if (n1 > 0) mma_ts<TC_F16>(tmem + (uint32_t)n0, a_op, bd + (uint64_t)n0 * 8u, idesc1_l1, 0u);
+                                    continue;
+                                }
+                                for (int grp = 0; grp < (n1 > 0 ? 2 : 1); ++grp) {
+                                    // column group grp: accumulator columns and B rows from n0 on for grp 1
+                                    const uint32_t dcol = grp ? tmem + (uint32_t)n0 : tmem;
+                                    const uint32_t id = grp ? idesc1 : idesc0;
+                                    const uint64_t goff = (uint64_t)(2 * g0) + (grp ? (uint64_t)n0 * 8u : 0u);
+                                    const uint64_t bk = bd + goff;
+                                    if (PARTS == 2 && cnt == 4) {
+                                        mma_k4x2(dcol, a_op, a_lo + acol, bk, id, acc);   // A_hi B_hi + A_lo B_hi
+                                        mma_k4<MODE>(dcol, a_op, bd_lo + goff, id, 1u);  // A_hi B_lo
+                                    } else if (cnt == 4) {
+                                        mma_k4<MODE>(dcol, a_op, bk, id, acc);
+                                    } else if (cnt == 2 && PARTS == 1) {
+                                        mma_k2<MODE>(dcol, a_op, bk, id, acc);
+                                    } else {  // a ragged last stage: one K-step at a time
+                                        for (int k = 0; k < cnt; ++k) {
+                                            const uint32_t ak = k == 0 ? acc : 1u;
+                                            mma_ts<MODE>(dcol, a_op + 8u * k, bk + 2u * k, id, ak);
+                                            if (PARTS == 2) {
+                                                mma_ts<MODE>(dcol, a_lo + acol + 8u * k, bk + 2u * k, id, 1u);
+                                                mma_ts<MODE>(dcol, a_op + 8u * k, bd_lo + goff + 2u * k, id, 1u);
+                                            }
                                         }
                                     }
                                 }
@@ -604,8 +617,8 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                         // the current one (waited for, unused) and those of layers l .. Dt still to come
                         mbar_arrive(smem_u32(&empty_bar[s]));
                         if (++s == (uint32_t)P.n_stages) { s = 0; ph ^= 1; }
-                        int rest = kb_n - 1;
-                        for (int l2 = l + 1; l2 <= Dt; ++l2) rest += (W + UPS - 1) / UPS;
+                        int rest = sb_n - 1;
+                        for (int l2 = l + 1; l2 <= Dt; ++l2) rest += ((W + UPS - 1) / UPS + KBS - 1) / KBS;
                         for (int k = 0; k < rest && ok; ++k) {
                             ok = mbar_wait(smem_u32(&full_bar[s]), ph, abort, hdr, 9, true);
                             if (!ok) break;

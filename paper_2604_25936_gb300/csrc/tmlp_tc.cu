@@ -225,7 +225,7 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
     P.L = L; P.W = W; P.D = fold1 ? 16 : D; P.l1_fold = fold1 ? 1 : 0; P.x_scale = x_scale; P.tail_kind = d.tail_kind; P.act = d.activation; P.enc = d.encoder; P.m = mf;
     P.first_mma = first;
     P.kpad = kpad;
-    P.stage_bytes = (uint32_t)parts * (uint32_t)W * 128u;  // one K-block of every part (hi and lo side by side)
+    P.stage_bytes = 2u * (uint32_t)W * 128u;  // hi and lo of one K-block, or two K-blocks of the one-part modes
     P.box_rows = box_rows;
     P.n_split = W <= 256 ? W : 176;
     {   // accumulator (W columns) + A_hi (W/2; FP8: ceil32(W)/4) [+ A_lo (W/2)], rounded up to a power of two
