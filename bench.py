@@ -445,6 +445,30 @@ def dynamic_bench(sand, model, x, n: int, local: int, steps: int):
     return res
 
 
+def grad_bench(sand, m, x, ws, n: int, steps: int):
+    """SDF and input gradient (a6) of the SAND query on the benchmark lattice: the tensor-core
+    path (value and three tangent rows per point, 32 points per 128-row tile) at float32 and
+    bf16, and the CUDA-core kernel beside them."""
+    import torch
+    stream = torch.cuda.current_stream()
+    res = {}
+    for prec in ("fp32", "bf16", "fp32_simt"):
+        for _ in range(2):
+            y, g = m.query_grad(x, precision=prec, workspace=ws)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps):
+            y, g = m.query_grad(x, precision=prec, workspace=ws)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / steps
+        res[prec] = {"ms": round(ms, 4), "queries_per_s": n / (ms / 1e3)}
+    res["kernels"] = {"fp32": "tmlp_tc_kernel<split, GRAD>", "bf16": "tmlp_tc_kernel<bf16, GRAD>",
+                      "fp32_simt": "tmlp_simt_kernel<GRAD>"}
+    return res
+
+
 def run_profile_case(args):
     """The same model and map as the benchmark on a smaller point set, for ncu captures."""
     import torch
@@ -625,6 +649,10 @@ def main():
     if rank == 0 and not args.no_variants:
         tr = trace_bench(sand, model, synth.scene_octree(7, N_LAYERS, far_field=True), local, max(3, K // 4))
 
+    gradb = None
+    if rank == 0 and not args.no_variants:
+        gradb = grad_bench(sand, m, x, ws, n, max(2, K // 8))
+
     dynb = None
     if rank == 0 and not args.no_variants:
         dynb = dynamic_bench(sand, model, x, n, local, max(2, K // 8))
@@ -675,6 +703,7 @@ def main():
         "sphere_trace": tr,
         "depth_map_build": mapb,
         "dynamic_exit": dynb,
+        "gradient": gradb,
         "serve_p99_ms": (serve or {}).get("bf16", {}).get("load_0.8", {}).get("p99_ms"),
     }
     if rank == 0:

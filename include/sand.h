@@ -152,8 +152,13 @@ sand_status sand_query_sdf(sand_model m, const float *d_points, int64_t n, float
                            const sand_query_opts *opts, void *stream);
 
 /* As sand_query_sdf, plus the input gradient d_grad[i] = dy/dx at x_i (surface
- * normal direction for sphere tracing); zero for exit layer 0.  d_out may be
- * NULL.  d_grad: device float32 [n][3]. */
+ * normal direction for sphere tracing); zero for exit layer 0, NaN for points
+ * outside the domain.  d_out may be NULL in full-depth mode only (a SAND query
+ * writes the stored far values there: SAND_EINVAL).  d_grad: device float32
+ * [n][3].  Every precision takes gradients: the tensor-core modes carry three
+ * tangent rows per point through the same MMAs as the value row (forward mode),
+ * SAND_FP32_SIMT runs the CUDA-core kernel; SAND_FP8 tangents are e4m3-rounded
+ * like the activations. */
 sand_status sand_query_sdf_grad(sand_model m, const float *d_points, int64_t n, float *d_out, float *d_grad,
                                 const sand_query_opts *opts, void *stream);
 

@@ -51,6 +51,7 @@ def _load():
             lib.oracle_eval.argtypes = [P, ctypes.c_double, P, P, ctypes.c_int64, P, ctypes.c_int, P, P, P]
             lib.oracle_query.argtypes = [P, ctypes.c_double, P, ctypes.c_int, P, P, P, P, ctypes.c_int64,
                                          ctypes.c_int, P, P, P]
+            lib.oracle_preact_margin.argtypes = [P, ctypes.c_double, P, P, ctypes.c_int64, P, ctypes.c_int, P]
             lib.oracle_param_count.argtypes = [P]
             lib.oracle_param_count.restype = ctypes.c_longlong
             lib.oracle_threads.restype = ctypes.c_int
@@ -122,6 +123,25 @@ def evaluate(model, points, depth, grad: bool = False, all_tails: bool = False):
     if all_tails:
         out.append(ys)
     return out[0] if len(out) == 1 else tuple(out)
+
+
+def preact_margin(model, points, depth):
+    """Per point, the smallest |u_l[j]| over the pre-activations u_l = W_l h_{l-1} + b_l of
+    layers 1..d (Eq. 1; +inf where d <= 0).  Where a ReLU network's gradient is compared
+    across two evaluations, points whose margin exceeds the pre-activation error take the
+    same ReLU decisions in both."""
+    hdr, w0, params = _model_args(model)
+    p = _pts(points)
+    n = p.shape[0]
+    out = np.empty(n, np.float64)
+    if np.isscalar(depth) or np.ndim(depth) == 0:
+        darr, cd = None, int(depth)
+    else:
+        darr, cd = np.ascontiguousarray(np.asarray(depth, np.int32)), 0
+    rc = _load().oracle_preact_margin(_ptr(hdr), w0, _ptr(params), _ptr(p), n, _ptr(darr), cd, _ptr(out))
+    if rc:
+        raise RuntimeError("oracle_preact_margin failed: %d" % rc)
+    return out
 
 
 def query(model, octree, points, max_depth: int = 0, grad: bool = False, exit_layers: bool = False):

@@ -242,6 +242,37 @@ int oracle_eval(const int32_t *hdr, double omega0, const float *params, const fl
     return bad ? -2 : 0;
 }
 
+/* Smallest |u_l[j]| over the pre-activations of layers 1..d of each point (Eq. 1:
+ * u_l = W_l h_{l-1} + b_l), +inf for d <= 0.  A ReLU network's gradient is discontinuous
+ * where some u_l[j] = 0; two evaluations whose u differ by less than margin[i] take the
+ * same ReLU decisions at point i. */
+int oracle_preact_margin(const int32_t *hdr, double omega0, const float *params, const float *pts, int64_t n,
+                         const int32_t *depth, int const_depth, double *margin) {
+    model_t M;
+    if (model_init(&M, hdr, omega0, params)) return -1;
+    int bad = 0;
+    #pragma omp parallel
+    {
+        double *work = (double *)malloc(sizeof(double) * work_doubles(&M));
+        double *ys = (double *)malloc(sizeof(double) * M.L);
+        if (!work || !ys) { bad = 1; }
+        #pragma omp for schedule(dynamic, 256)
+        for (int64_t i = 0; i < n; ++i) {
+            if (bad) continue;
+            int d = depth ? depth[i] : const_depth;
+            if (d > M.L) d = M.L;
+            margin[i] = INFINITY;
+            if (d <= 0) continue;
+            (void)eval_one(&M, pts + 3 * i, d, ys, NULL, work);
+            const double *U = work + 4 * (size_t)M.D;  /* eval_one's layout: h0 [D], J [3D], U [d][W] */
+            for (int64_t k = 0; k < (int64_t)d * M.W; ++k)
+                if (fabs(U[k]) < margin[i]) margin[i] = fabs(U[k]);
+        }
+        free(work); free(ys);
+    }
+    return bad ? -2 : 0;
+}
+
 /* The SAND query (Sec. 3.4): lookup, then the stored value for exit layer 0,
  * NaN for a NaN point, else y_d.  d_out (nullable) receives the exit layers
  * (-1 for NaN points).  grad (nullable) = d y / d x (0 for exit layer 0). */

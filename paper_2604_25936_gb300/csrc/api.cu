@@ -368,7 +368,10 @@ static sand_status run_query(sand_model m, const float *d_points, int64_t n, flo
     if (!o.full_depth && m->map_level < 0) { set_error("no depth map loaded"); return SAND_ENOMAP; }
     if (o.full_depth && o.d_exit_layers) { set_error("exit layers are not produced in full-depth mode"); return SAND_EINVAL; }
     if (o.full_depth && d_count) { set_error("full-depth mode needs a host point count"); return SAND_EINVAL; }
-    const bool simt = o.precision == SAND_FP32_SIMT || d_grad != nullptr;
+    // gradients run on the tensor cores too; the CUDA-core kernel serves SAND_FP32_SIMT, and
+    // float32 gradients of widths the tensor-core path does not take
+    const bool simt = o.precision == SAND_FP32_SIMT ||
+                      (d_grad != nullptr && o.precision == SAND_FP32 && !tc_supported(m->desc, o.precision));
     if (o.all_tails && simt) { set_error("all_tails runs on the tensor-core precisions only"); return SAND_EUNSUPPORTED; }
     if (!simt && !tc_supported(m->desc, o.precision)) {
         set_error("precision %d is not supported for this model on the tensor-core path", o.precision);
@@ -404,7 +407,8 @@ static sand_status run_query(sand_model m, const float *d_points, int64_t n, flo
     } else {
         st = tc_prepare(&m->tc, m->desc, m->params.data(), o.precision);
         if (st) return st;
-        SAND_CUDA(launch_tmlp_tc(m->tc, m->simt, d_points, n, o.full_depth, ws, d_out, m->num_sms, s, o.all_tails),
+        SAND_CUDA(launch_tmlp_tc(m->tc, m->simt, d_points, n, o.full_depth, ws, d_out, m->num_sms, s, o.all_tails, 0.f,
+                                 nullptr, d_grad),
                   "tensor-core T-MLP kernel");
     }
     if (ev) SAND_CUDA(cudaEventRecord(ev[2], s), "event record");

@@ -16,9 +16,10 @@ bool tc_supported(const sand_tmlp_desc &d, int precision);
 sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params, int precision);
 // all_tails (with full_depth): out[i * L + l - 1] = y_l for every layer l of every point.
 // dyn_r > 0 (with full_depth): octree-free dynamic exit at |t_l| < dyn_r, exit layers to exit_out.
+// grad: also dy/dx per point ([n][3], forward-mode tangents as three more rows per point).
 cudaError_t launch_tmlp_tc(const TcModel &tc, const TmlpDev &M, const float *pts, int64_t n, int full_depth, void *ws,
                            float *out, int num_sms, cudaStream_t s, int all_tails = 0, float dyn_r = 0.f,
-                           uint8_t *exit_out = nullptr);
+                           uint8_t *exit_out = nullptr, float *grad = nullptr);
 void tc_release(TcModel *tc);
 
 }  // namespace sand

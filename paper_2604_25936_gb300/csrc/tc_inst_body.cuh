@@ -1,6 +1,6 @@
 // One instantiation of the tensor-core T-MLP kernel per activation and tail kind, for the
-// precision mode SAND_INST_MODE and the extended-output switch SAND_INST_EXT (set by the
-// including translation unit).
+// precision mode SAND_INST_MODE and the kernel variant SAND_INST_VAR (0 plain, 1 extended
+// outputs, 2 gradient), set by the including translation unit.
 #include "tc_kernel.cuh"
 
 namespace sand {
@@ -9,7 +9,7 @@ template <int ACT, int TAIL>
 static cudaError_t launch_one(const CUtensorMap &map, const TcParams &P, const float *pts, const float4 *sorted,
                               WsHeader *hdr, int64_t n, int full_depth, float *out, int grid, size_t smem,
                               cudaStream_t s) {
-    auto kern = tmlp_tc_kernel<SAND_INST_MODE, ACT, TAIL, SAND_INST_EXT>;
+    auto kern = tmlp_tc_kernel<SAND_INST_MODE, ACT, TAIL, SAND_INST_VAR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, kTcThreads, smem, s>>>(map, P, pts, sorted, hdr, n, full_depth, out);
@@ -17,7 +17,7 @@ static cudaError_t launch_one(const CUtensorMap &map, const TcParams &P, const f
 }
 
 template <>
-cudaError_t launch_tc_mode<SAND_INST_MODE, SAND_INST_EXT>(const CUtensorMap &map, const TcParams &P, int act, int tail,
+cudaError_t launch_tc_mode<SAND_INST_MODE, SAND_INST_VAR>(const CUtensorMap &map, const TcParams &P, int act, int tail,
                                                           const float *pts, const float4 *sorted, WsHeader *hdr,
                                                           int64_t n, int full_depth, float *out, int grid,
                                                           size_t smem, cudaStream_t s) {

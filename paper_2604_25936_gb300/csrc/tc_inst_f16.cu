@@ -1,4 +1,4 @@
 // Tensor-core T-MLP kernel instantiations: the fp16 mode.
 #define SAND_INST_MODE TC_F16
-#define SAND_INST_EXT false
+#define SAND_INST_VAR 0
 #include "tc_inst_body.cuh"

@@ -1,4 +1,4 @@
 // Tensor-core T-MLP kernel instantiations: the float32 mode (3 x fp16 split), extended outputs (all tails, dynamic exit).
 #define SAND_INST_MODE TC_SPLIT16
-#define SAND_INST_EXT true
+#define SAND_INST_VAR 1
 #include "tc_inst_body.cuh"

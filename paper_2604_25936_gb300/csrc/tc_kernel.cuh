@@ -89,6 +89,7 @@ struct TcParams {
     float dyn_r;              // > 0: octree-free dynamic exit (full depth): a row stops at the first layer whose
                               // tail |t_l| < dyn_r; a tile stops issuing MMAs once all its rows have stopped
     uint8_t *exit_out;        // dynamic exit: the layer each row stopped at (optional)
+    float *grad;              // gradient variant: dy/dx per point, [n][3]
     int kpad;                 // padded K of the packed weight matrix (multiple of 64; of 128 in the FP8 mode)
     int n_stages;
     uint32_t stage_bytes;     // parts x W x 128: one K-block of the weights (hi and lo in the float32 mode)
@@ -348,9 +349,13 @@ __device__ __forceinline__ void tmem_st_half(uint32_t taddr, const uint32_t *v) 
 // ------------------------------------------------------------------ the kernel
 // 16 accumulator values (units c0 .. c0+15) of this thread's row: bias, activation,
 // tail partial sums and, when write_a, the packed activations into TMEM (A operand).
-template <int MODE, int ACT, int TAIL>
+// GRAD: the four rows of a point (lanes 4p .. 4p+3 of a warp) carry its value (is_val) and the
+// derivatives along x, y, z of every activation (forward-mode tangents): a tangent row's
+// pre-activation is the derivative of the value row's, without the bias; its activation is
+// cos(u) du (sine, one hardware sine of u + pi/2 for the point's u) or [u > 0] du (ReLU).
+template <int MODE, int ACT, int TAIL, bool GRAD = false>
 __device__ __forceinline__ void epilogue16(const float *cs, int W, float c1, const uint32_t *v, int c0, bool write_a,
-                                           uint32_t a_hi, uint32_t a_lo, float &sa, float &sb) {
+                                           uint32_t a_hi, uint32_t a_lo, float &sa, float &sb, bool is_val = true) {
     constexpr bool MULT = TAIL == SAND_TAIL_MULT;
     uint32_t phi[8], plo[8], p8[4];
 #pragma unroll
@@ -372,7 +377,19 @@ __device__ __forceinline__ void epilogue16(const float *cs, int W, float c1, con
         float h8[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const float hv = activate<ACT>(fmaf(__uint_as_float(v[8 * g + i]), c1, bv[i]));
+            float hv;
+            if (!GRAD) {
+                hv = activate<ACT>(fmaf(__uint_as_float(v[8 * g + i]), c1, bv[i]));
+            } else {
+                const float u = fmaf(__uint_as_float(v[8 * g + i]), c1, is_val ? bv[i] : 0.f);
+                const float uv = __shfl_sync(0xffffffffu, u, (threadIdx.x & 31) & ~3);  // the point's u
+                if (ACT == SAND_ACT_RELU) {
+                    hv = is_val ? fmaxf(u, 0.f) : (uv > 0.f ? u : 0.f);
+                } else {
+                    const float sv = __sinf(is_val ? u : uv + 1.57079632679489662f);
+                    hv = is_val ? sv : sv * u;
+                }
+            }
             h8[i] = hv;
             sa = fmaf(av[i], hv, sa);
             if (MULT) sb = fmaf(tbv[i], hv, sb);
@@ -395,12 +412,15 @@ __device__ __forceinline__ void epilogue16(const float *cs, int W, float c1, con
     }
 }
 
-template <int MODE, int ACT, int TAIL, bool EXT>
+template <int MODE, int ACT, int TAIL, int VAR>
 __global__ void __launch_bounds__(kTcThreads, 1)
 tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const float *__restrict__ pts,
                const float4 *__restrict__ sorted, WsHeader *hdr, int64_t n, int full_depth, float *__restrict__ out) {
     constexpr int PARTS = MODE == TC_SPLIT16 ? 2 : 1;
     constexpr bool MULT = TAIL == SAND_TAIL_MULT;
+    constexpr bool EXT = VAR == 1;   // extended outputs: all tails, dynamic exit
+    constexpr bool GRAD = VAR == 2;  // value and input gradient: 32 points x 4 rows per tile
+    constexpr int PPT = GRAD ? kTileM / 4 : kTileM;  // points per tile
     constexpr int UPS = MODE == TC_FP8 ? 128 : 64;  // K-units per weight stage (one 128-byte row per unit)
     constexpr int UPK = MODE == TC_FP8 ? 32 : 16;   // K-units per MMA (32 bytes of every row)
     // A stage holds two W x 128-byte sub-blocks: the hi and lo weights of one K-block (float32
@@ -429,8 +449,8 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n_rows = full_depth ? n : (int64_t)hdr->n_active;
-    const int64_t n_tiles = (n_rows + kTileM - 1) / kTileM;
-    auto tile_depth = [&](int64_t t) -> int { return full_depth ? L : tc_row_depth(hdr, (uint32_t)(t * kTileM), L); };
+    const int64_t n_tiles = (n_rows + PPT - 1) / PPT;
+    auto tile_depth = [&](int64_t t) -> int { return full_depth ? L : tc_row_depth(hdr, (uint32_t)(t * PPT), L); };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < P.n_stages; ++s) {
@@ -702,7 +722,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
         // this thread's row of tile tt: coordinates, exit layer, original index (-1 for padding)
         auto load_row = [&](int64_t tt) {
             TcRow a{0.f, 0.f, 0.f, 0, -1};
-            const int64_t row = tt * kTileM + r;
+            const int64_t row = GRAD ? tt * PPT + (r >> 2) : tt * kTileM + r;  // GRAD: 4 rows per point
             if (tt < n_tiles && row < n_rows) {
                 if (full_depth) {
                     a.idx = row;
@@ -757,8 +777,18 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             float y = 0.f;
             bool alive = idx >= 0;  // dynamic exit: this row still runs
             // ---- the A operand of layer 1: split coordinates, or the Fourier features
+            const int comp = GRAD ? (r & 3) : 0;  // GRAD: 0 = value row, 1..3 = d/dx, d/dy, d/dz row
+            const bool is_val = comp == 0;
             if (P.l1_fold) {
-                put_a1(cur);
+                // the tangent of the input is a unit vector; one call for the whole warp (put_a1
+                // holds warp-collective TMEM stores), the row selected per lane
+                TcRow a1 = cur;
+                if (GRAD && !is_val) {
+                    a1.x0 = comp == 1 ? 1.f : 0.f;
+                    a1.x1 = comp == 2 ? 1.f : 0.f;
+                    a1.x2 = comp == 3 ? 1.f : 0.f;
+                }
+                put_a1(a1);
             } else {
                 // Fourier features gamma(x) = [sin 2 pi s, cos 2 pi s]; in_dim == W, same slices as the layers
                 for (int kb = 0; kb < KB; ++kb) {
@@ -771,7 +801,10 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                             const float ph = fourier_phase(P.B + 3 * kk, x0, x1, x2);
                             float sv, cv;
                             sincospif(2.0f * ph, &sv, &cv);
-                            h8[i] = k < P.m ? sv : cv;
+                            // tangent rows: d gamma / dx_c = 2 pi B_kc (cos, -sin)
+                            const float bk = GRAD ? P.B[3 * kk + (is_val ? 0 : comp - 1)] : 0.f;
+                            const float tv = 6.28318530717958647692f * bk * (k < P.m ? cv : -sv);
+                            h8[i] = (GRAD && !is_val) ? tv : (k < P.m ? sv : cv);
                         }
                         st_a8(k0, h8);
                     }
@@ -797,7 +830,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                             uint32_t v[16];
                             tmem_ld16(t_lane + (uint32_t)c0, v);
                             tmem_wait_ld();
-                            epilogue16<MODE, ACT, TAIL>(cs, W, c1, v, c0, !last, a_hi_l, a_lo_l, sa, sb);
+                            epilogue16<MODE, ACT, TAIL, GRAD>(cs, W, c1, v, c0, !last, a_hi_l, a_lo_l, sa, sb, is_val);
                         }
                         if (!last && !dyn) signal(&a_ready[kb], true);
                     }
@@ -811,23 +844,37 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
 #pragma unroll
                     for (int kb = 1; kb < 4; ++kb)
                         if (kb < KB) tmem_ld32(t_lane + (uint32_t)(64 * kb + su0), v[kb]);
-                    epilogue16<MODE, ACT, TAIL>(cs, W, c1, v[0], su0, !last, a_hi_l, a_lo_l, sa, sb);
-                    epilogue16<MODE, ACT, TAIL>(cs, W, c1, v[0] + 16, su0 + 16, !last, a_hi_l, a_lo_l, sa, sb);
+                    epilogue16<MODE, ACT, TAIL, GRAD>(cs, W, c1, v[0], su0, !last, a_hi_l, a_lo_l, sa, sb, is_val);
+                    epilogue16<MODE, ACT, TAIL, GRAD>(cs, W, c1, v[0] + 16, su0 + 16, !last, a_hi_l, a_lo_l, sa, sb, is_val);
                     tmem_wait_ld();
                     signal(d_drained, false);  // the next layer may overwrite the accumulator
                     if (!last && !dyn) signal(&a_ready[0], true);
 #pragma unroll
                     for (int kb = 1; kb < 4; ++kb) {
                         if (kb < KB) {
-                            epilogue16<MODE, ACT, TAIL>(cs, W, c1, v[kb], 64 * kb + su0, !last, a_hi_l, a_lo_l, sa, sb);
-                            epilogue16<MODE, ACT, TAIL>(cs, W, c1, v[kb] + 16, 64 * kb + su0 + 16, !last, a_hi_l, a_lo_l,
-                                                        sa, sb);
+                            epilogue16<MODE, ACT, TAIL, GRAD>(cs, W, c1, v[kb], 64 * kb + su0, !last, a_hi_l, a_lo_l, sa, sb, is_val);
+                            epilogue16<MODE, ACT, TAIL, GRAD>(cs, W, c1, v[kb] + 16, 64 * kb + su0 + 16, !last, a_hi_l,
+                                                              a_lo_l, sa, sb, is_val);
                             if (!last && !dyn) signal(&a_ready[kb], true);
                         }
                     }
                 }
                 exchange(sa, sb);
-                if (slice == 0) {
+                if (GRAD && slice == 0) {
+                    // value row: the tail; tangent row: its derivative (product rule for Eq. 3);
+                    // y holds the value, or the gradient component along x_comp
+                    const float sa_v = __shfl_sync(0xffffffffu, sa, lane & ~3);
+                    const float sb_v = __shfl_sync(0xffffffffu, sb, lane & ~3);
+                    const float tb0 = __ldg(P.tb + 2 * (l - 1)), tb1 = __ldg(P.tb + 2 * (l - 1) + 1);
+                    float tl;
+                    if (is_val) tl = (MULT && l >= 2) ? (sa + tb0) * (sb + tb1) : sa + tb0;
+                    else tl = (MULT && l >= 2) ? sa * (sb_v + tb1) + (sa_v + tb0) * sb : sa;
+                    y += tl;
+                    if (d == l && idx >= 0) {
+                        if (!is_val) P.grad[3 * idx + comp - 1] = y;
+                        else if (out) out[idx] = y;  // a full-depth gradient query may omit the values
+                    }
+                } else if (slice == 0) {
                     const float t0v = sa + __ldg(P.tb + 2 * (l - 1));
                     float tl = t0v;
                     if (MULT && l >= 2) tl = t0v * (sb + __ldg(P.tb + 2 * (l - 1) + 1));
@@ -867,10 +914,11 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
     }
 }
 
-// Launch one instantiation (defined in the per-mode translation units).  EXT: the extended
-// outputs (all tails, dynamic exit) are compiled in; the plain query path carries none of
-// their code, which its single MMA-issuing thread would otherwise pay for at every layer.
-template <int MODE, bool EXT>
+// Launch one instantiation (defined in the per-mode translation units).  VAR 0: the plain
+// query; 1: the extended outputs (all tails, dynamic exit); 2: value and input gradient.
+// The plain query path carries none of the others' code, which its single MMA-issuing
+// thread would otherwise pay for at every layer.
+template <int MODE, int VAR>
 cudaError_t launch_tc_mode(const CUtensorMap &map, const TcParams &P, int act, int tail, const float *pts,
                            const float4 *sorted, WsHeader *hdr, int64_t n, int full_depth, float *out, int grid,
                            size_t smem, cudaStream_t s);

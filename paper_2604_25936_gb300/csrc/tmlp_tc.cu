@@ -258,7 +258,8 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
 }
 
 cudaError_t launch_tmlp_tc(const TcModel &tc, const TmlpDev &M, const float *pts, int64_t n, int full_depth, void *ws,
-                           float *out, int num_sms, cudaStream_t s, int all_tails, float dyn_r, uint8_t *exit_out) {
+                           float *out, int num_sms, cudaStream_t s, int all_tails, float dyn_r, uint8_t *exit_out,
+                           float *grad) {
     (void)M;
     TcPack *pk = static_cast<TcPack *>(tc.host);
     if (!pk) return cudaErrorInvalidValue;
@@ -266,19 +267,22 @@ cudaError_t launch_tmlp_tc(const TcModel &tc, const TmlpDev &M, const float *pts
     P.all_tails = all_tails && full_depth ? 1 : 0;
     P.dyn_r = full_depth && !P.all_tails ? dyn_r : 0.f;
     P.exit_out = P.dyn_r > 0.f ? exit_out : nullptr;
+    P.grad = P.all_tails || P.dyn_r > 0.f ? nullptr : grad;
     WsLayout Lw = ws_layout(full_depth ? 0 : n);
     char *base = static_cast<char *>(ws);
     WsHeader *hdr = reinterpret_cast<WsHeader *>(base);
     const float4 *sorted = full_depth ? nullptr : reinterpret_cast<const float4 *>(base + Lw.sorted);
     const int parts = pk->mode == TC_SPLIT16 ? 2 : 1;
     const size_t smem = tc_smem_bytes(P, parts);
-    const int64_t tiles = (n + kTileM - 1) / kTileM;
+    const int64_t ppt = P.grad ? kTileM / 4 : kTileM;  // points per tile (gradient: 4 rows per point)
+    const int64_t tiles = (n + ppt - 1) / ppt;
     int grid = num_sms;
     if (tiles < grid) grid = (int)(tiles > 0 ? tiles : 1);
-    const bool ext = P.all_tails || P.dyn_r > 0.f;
-#define SAND_LAUNCH(M)                                                                                              \
-    (ext ? launch_tc_mode<M, true>(pk->map, P, P.act, P.tail_kind, pts, sorted, hdr, n, full_depth, out, grid, smem, s) \
-         : launch_tc_mode<M, false>(pk->map, P, P.act, P.tail_kind, pts, sorted, hdr, n, full_depth, out, grid, smem, s))
+    const int var = P.grad ? 2 : (P.all_tails || P.dyn_r > 0.f) ? 1 : 0;
+#define SAND_LAUNCH(M)                                                                                                  \
+    (var == 2   ? launch_tc_mode<M, 2>(pk->map, P, P.act, P.tail_kind, pts, sorted, hdr, n, full_depth, out, grid, smem, s) \
+     : var == 1 ? launch_tc_mode<M, 1>(pk->map, P, P.act, P.tail_kind, pts, sorted, hdr, n, full_depth, out, grid, smem, s) \
+                : launch_tc_mode<M, 0>(pk->map, P, P.act, P.tail_kind, pts, sorted, hdr, n, full_depth, out, grid, smem, s))
     switch (pk->mode) {
         case TC_SPLIT16: return SAND_LAUNCH(TC_SPLIT16);
         case TC_F16: return SAND_LAUNCH(TC_F16);

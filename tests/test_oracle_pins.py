@@ -327,3 +327,36 @@ def test_gradient_matches_torch_autograd():
     Y = torch.stack(outs, 1)[torch.arange(100), torch.tensor(depth - 1)]
     (gx,) = torch.autograd.grad(Y.sum(), x)
     np.testing.assert_allclose(g, gx.numpy(), rtol=0, atol=1e-11)
+
+
+def test_preact_margin_closed_form():
+    """The hand-built ReLU sphere model (width 6): layer 1's pre-activations are +-x, +-y, +-z,
+    so the margin at exit layer 1 is min(|x|, |y|, |z|); layer 2 is the identity on ReLU(+-x, ...),
+    half of which are exactly 0, so from layer 2 on the margin is 0; exit layer 0 gives +inf."""
+    model = synth.relu_sphere_tmlp(0.6, width=6)
+    pts = synth.uniform_points(500, seed=9)
+    p = pts.astype(np.float64)
+    np.testing.assert_array_equal(oracle.preact_margin(model, pts, 1), np.abs(p).min(1))
+    np.testing.assert_array_equal(oracle.preact_margin(model, pts, 3), np.zeros(500))
+    d = np.array([0, 1, 2] * 166 + [1, 1], np.int32)
+    m = oracle.preact_margin(model, pts, d)
+    assert np.isinf(m[d == 0]).all()
+    np.testing.assert_array_equal(m[d == 1], np.abs(p[d == 1]).min(1))
+
+
+def test_preact_margin_brute_force():
+    """Against layer-by-layer float64 numpy on a small random ReLU Fourier-feature model."""
+    model = synth.relu_ff_tmlp(3, 16, n_freq=8, sigma=2.0, seed=4)
+    pts = synth.uniform_points(64, seed=2)
+    x = pts.astype(np.float64)
+    ph = x @ model.enc_B.astype(np.float64).T
+    h = np.concatenate([np.sin(2 * np.pi * ph), np.cos(2 * np.pi * ph)], 1)
+    mins = []
+    for l in range(3):
+        Wl = model.W1 if l == 0 else model.Wh[l - 1]
+        bl = model.b1 if l == 0 else model.bh[l - 1]
+        u = h @ Wl.astype(np.float64).T + bl.astype(np.float64)
+        mins.append(np.abs(u).min(1))
+        h = np.maximum(u, 0.0)
+    for d in (1, 2, 3):
+        np.testing.assert_allclose(oracle.preact_margin(model, pts, d), np.min(mins[:d], 0), rtol=1e-9, atol=1e-12)
