@@ -492,6 +492,115 @@ def run_profile_case(args):
     return 0
 
 
+def _best_ms(fn, reps: int = 10, warm: int = 3) -> float:
+    """Shortest of `reps` CUDA-event timings of fn() on the current stream, after `warm` calls."""
+    import torch
+    stream = torch.cuda.current_stream()
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        best = min(best, a.elapsed_time(b))
+    return best
+
+
+def _sustained_ms(fn, seconds: float = 2.0) -> float:
+    """Mean CUDA-event time per call of fn() run back to back for about `seconds`."""
+    import torch
+    stream = torch.cuda.current_stream()
+    calls = max(1, int(seconds * 1e3 / max(_best_ms(fn, reps=2, warm=1), 1e-3)))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(calls):
+        fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / calls
+
+
+def sin_rate(sand, local: int) -> float:
+    """Hardware sines per second (sand_probe_rate, one 8 x 256-thread-block wave per SM)."""
+    import torch
+    nb = torch.cuda.get_device_properties(local).multi_processor_count * 8
+    iters = 1 << 14
+    sink = torch.empty(nb * sand.binding.PROBE_THREADS, dtype=torch.float32, device="cuda")
+    ms = _best_ms(lambda: sand.binding.probe_rate(sand.binding.PROBE_SIN, nb, iters, sink))
+    return sand.binding.PROBE_CHAINS * iters * sand.binding.PROBE_THREADS * nb / (ms / 1e3)
+
+
+def run_peaks(args):
+    """Measured throughput of the units behind the kernels' rooflines, on this GPU: cuBLAS
+    GEMMs at 8192^3 (bf16, fp16, TF32, float32 SGEMM, FP8 e4m3 through torch._scaled_mm),
+    burst (best of 10) and sustained (back to back for 2 s), and the float32 FMA and
+    hardware-sine issue rates of sand_probe_rate.  One JSON line."""
+    import torch
+    import paper_2604_25936_gb300 as sand
+    from paper_2604_25936_gb300 import build as sand_build
+    sand_build.build()
+    torch.cuda.set_device(0)
+    props = torch.cuda.get_device_properties(0)
+    uuid = None
+    try:
+        uuid = str(props.uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    res = {"peaks": props.name, "sm_count": props.multi_processor_count, "gemm_n": 8192}
+    N = 8192
+    flop = 2.0 * N ** 3
+    g = torch.Generator(device="cuda").manual_seed(0)
+    a32 = torch.randn(N, N, device="cuda", generator=g)
+    b32 = torch.randn(N, N, device="cuda", generator=g)
+    cases = {"bf16": lambda: torch.matmul(a16b, b16b), "fp16": lambda: torch.matmul(a16h, b16h),
+             "tf32": lambda: torch.matmul(a32, b32), "fp32_sgemm": lambda: torch.matmul(a32, b32)}
+    a16b, b16b = a32.bfloat16(), b32.bfloat16()
+    a16h, b16h = a32.half(), b32.half()
+    for name, fn in cases.items():
+        torch.backends.cuda.matmul.allow_tf32 = name == "tf32"
+        try:
+            burst = _best_ms(fn)
+            sus = _sustained_ms(fn)
+            res[name + "_tflops"] = round(flop / (burst / 1e3) / 1e12, 1)
+            res[name + "_tflops_sustained"] = round(flop / (sus / 1e3) / 1e12, 1)
+        except Exception as e:  # a library path missing on this build of torch
+            res[name + "_tflops"] = None
+            res[name + "_error"] = str(e)[:200]
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        a8 = a32.clamp(-8, 8).to(torch.float8_e4m3fn)
+        b8 = b32.clamp(-8, 8).to(torch.float8_e4m3fn).t().contiguous().t()  # column-major second operand
+        one = torch.ones((), device="cuda")
+        fn = lambda: torch._scaled_mm(a8, b8, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+        burst, sus = _best_ms(fn), _sustained_ms(fn)
+        res["fp8_tflops"] = round(flop / (burst / 1e3) / 1e12, 1)
+        res["fp8_tflops_sustained"] = round(flop / (sus / 1e3) / 1e12, 1)
+    except Exception as e:
+        res["fp8_tflops"] = None
+        res["fp8_error"] = str(e)[:200]
+    del a32, b32, a16b, b16b, a16h, b16h
+    nb = props.multi_processor_count * 8
+    sink = torch.empty(nb * sand.binding.PROBE_THREADS, dtype=torch.float32, device="cuda")
+    it = 1 << 16
+    ms = _best_ms(lambda: sand.binding.probe_rate(sand.binding.PROBE_FFMA, nb, it, sink))
+    res["ffma_tflops"] = round(2.0 * sand.binding.PROBE_CHAINS * it * sand.binding.PROBE_THREADS * nb / (ms / 1e3) / 1e12, 2)
+    res["sin_per_s"] = sin_rate(sand, 0)
+    ck = clocks.stop()
+    res["clocks"] = ck
+    if ck and ck.get("sm_mhz"):
+        mhz = ck["sm_mhz"]
+        res["ffma_per_clk_per_sm"] = round(res["ffma_tflops"] * 1e12 / 2 / (mhz * 1e6) / props.multi_processor_count, 1)
+        res["sin_per_clk_per_sm"] = round(res["sin_per_s"] / (mhz * 1e6) / props.multi_processor_count, 2)
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -507,9 +616,12 @@ def main():
                          "queries on grid^3 uniform points; prints one line")
     ap.add_argument("--grid", type=int, default=GRID)
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="length of each open-loop serving run (0 = skip)")
+    ap.add_argument("--peaks", action="store_true", help="measure GEMM, FMA and sine peaks of this GPU; prints one line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.peaks:
+        return run_peaks(args)
     if args.profile:
         return run_profile_case(args)
 
@@ -635,6 +747,12 @@ def main():
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": kernel_traffic(prec), "kernel": KERNEL_NAME[prec],
                 "peak_source": "%s bf16 sustained %.1f TFLOP/s x %.3g (%s)" % (pk_src, base, ratio, prec)}
+    # the epilogue's co-bound: one hardware sine per unit per row-layer (Eq. 2), against the
+    # issue rate sand_probe_rate measures on this GPU in this run
+    sines = float((np.arange(N_LAYERS + 1) * WIDTH * counts).sum())
+    sr = sin_rate(sand, local)
+    epi = {"unit": "sines/s", "achieved": sines / (mlp_avg / 1e3), "peak": sr, "frac": sines / (mlp_avg / 1e3) / sr,
+           "sines_per_launch": sines, "peak_source": "sand_probe_rate(SAND_PROBE_SIN), measured in this run"}
 
     # ---- serving: continuous batching over three resident models (rank 0 only)
     serve = None
@@ -694,6 +812,7 @@ def main():
         "stage_ms": {"lookup_bin": sum(pre_ms) / K, "tmlp": mlp_avg},
         "exit_layer_histogram": hist,
         "roofline": roof,
+        "epilogue_pipe": epi,
         "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": 12 * n, "d2h_bytes_per_step": 4 * n},
         "gpu_launches": 4 * K,
         "clocks": clocks,

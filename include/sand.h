@@ -67,7 +67,7 @@ typedef enum {
 } sand_precision;
 
 typedef enum { SAND_TAIL_LINEAR = 0, SAND_TAIL_MULT = 1 } sand_tail_kind;
-typedef enum { SAND_ACT_SINE = 0, SAND_ACT_RELU = 1 } sand_activation;
+typedef enum { SAND_ACT_SINE = 0, SAND_ACT_RELU = 1, SAND_ACT_FINER = 2 } sand_activation;
 typedef enum { SAND_ENC_NONE = 0, SAND_ENC_FOURIER = 1 } sand_encoder;
 
 /* Shape of a T-MLP (Eq. 2 / Eq. 3).
@@ -75,7 +75,10 @@ typedef enum { SAND_ENC_NONE = 0, SAND_ENC_FOURIER = 1 } sand_encoder;
  *   width     W, hidden units per layer (16 .. 512)
  *   in_dim    3 without an encoder, 2 * n_freq with Fourier features
  *   activation SAND_ACT_SINE: h = sin(omega0 * (W h + b)) (SIREN);
- *             SAND_ACT_RELU: h = max(0, W h + b)
+ *             SAND_ACT_RELU: h = max(0, W h + b);
+ *             SAND_ACT_FINER: h = sin(omega0 * (|z| + 1) * z), z = W h + b, the
+ *             variable-periodic sine of the FINER backbone (Sec. 2 cites it, the
+ *             SAND-FINER rows of Table 1 use it; the formula is FINER's own)
  *   encoder   SAND_ENC_FOURIER: h_0 = [sin(2 pi B x), cos(2 pi B x)], B [n_freq][3]
  *   tail_kind SAND_TAIL_MULT: t_i = (a_i.h_i + c_i)(b_i.h_i + e_i) for i >= 2 (Eq. 3);
  *             tail 1 is always affine.                                          */
@@ -305,6 +308,20 @@ sand_status sand_server_wait(sand_server s, uint64_t ticket, double timeout_s, d
 sand_status sand_server_stats(sand_server s, sand_server_report *out);
 /* Finish queued work, stop the threads, release streams and the arena. */
 sand_status sand_server_destroy(sand_server s);
+
+/* ---- issue-rate probes (the roofline denominators of the epilogue pipes) ----
+ * Launch n_blocks x 256 threads on `device` and `stream`; each thread runs 8
+ * independent chains of `iters` steps and writes one float to d_sink (device,
+ * n_blocks x 256 floats, 4-byte aligned; the values carry no meaning).
+ *   SAND_PROBE_FFMA: one float32 fused multiply-add per step and chain, so
+ *     2 x 8 x iters x 256 x n_blocks FLOP per launch;
+ *   SAND_PROBE_SIN: one hardware sine of a radian argument (the form the sine
+ *     activations of Eq. 2 take) and one multiply per step and chain, so
+ *     8 x iters x 256 x n_blocks sines per launch.
+ * Asynchronous: time it with events on `stream`.  SAND_EINVAL for an unknown
+ * kind, n_blocks outside 1..2^20, iters <= 0 or a bad d_sink. */
+typedef enum { SAND_PROBE_FFMA = 0, SAND_PROBE_SIN = 1 } sand_probe_kind;
+sand_status sand_probe_rate(int kind, int device, int n_blocks, int iters, float *d_sink, void *stream);
 
 /* Describe a loaded model. */
 sand_status sand_model_desc(sand_model m, sand_tmlp_desc *out);

@@ -14,7 +14,12 @@
  *     centre.  Level of detail (Sec. 3.4): d <- min(d, max_depth) when d > 0
  *     and max_depth > 0.  A NaN coordinate yields exit layer -1 and NaN.
  *   - T-MLP (Eq. 2): h_0 = x (or Fourier features of x), h_i = act(W_i h_{i-1}
- *     + b_i) with act = sin(omega0 * .) (SIREN) or max(0, .) (ReLU),
+ *     + b_i) with act = sin(omega0 * .) (SIREN), max(0, .) (ReLU) or
+ *     sin(omega0 (|.| + 1) .) (FINER, the variable-periodic sine of the
+ *     SAND-FINER backbone; SAND cites FINER without restating its formula, so
+ *     this activation is PARITY UNPINNED against the paper: its tests check
+ *     only self-consistency — the gradient against central differences, the
+ *     small-argument limit where it becomes SIREN, the sign symmetry),
  *     t_i = a_i . h_i + c_i, and for multiplicative tails (Eq. 3) with i >= 2
  *     t_i = (a_i . h_i + c_i) (b_i . h_i + e_i); y_i = y_{i-1} + t_i, y_0 = 0.
  *     The result for exit layer d is y_d.
@@ -37,6 +42,7 @@
 
 #define ORACLE_TAIL_MULT 1
 #define ORACLE_ACT_RELU 1
+#define ORACLE_ACT_FINER 2
 #define ORACLE_ENC_FOURIER 1
 
 typedef struct {
@@ -160,7 +166,9 @@ static double eval_one(const model_t *M, const float *x, int d, double *ys, doub
         double *u = U + (size_t)(l - 1) * W, *h = H + (size_t)(l - 1) * W;
         for (int j = 0; j < W; ++j) {
             u[j] = dot_f(Wl + (size_t)j * fan, hp, fan) + (double)bl[j];
-            h[j] = (M->act == ORACLE_ACT_RELU) ? (u[j] > 0.0 ? u[j] : 0.0) : sin(M->omega0 * u[j]);
+            if (M->act == ORACLE_ACT_RELU) h[j] = u[j] > 0.0 ? u[j] : 0.0;
+            else if (M->act == ORACLE_ACT_FINER) h[j] = sin(M->omega0 * (fabs(u[j]) + 1.0) * u[j]);
+            else h[j] = sin(M->omega0 * u[j]);
         }
         const float *a = M->tw + (size_t)(l - 1) * 2 * W, *b = a + W;
         double t0 = dot_f(a, h, W) + (double)M->tb[(l - 1) * 2];
@@ -184,8 +192,11 @@ static double eval_one(const model_t *M, const float *x, int d, double *ys, doub
                 for (int j = 0; j < W; ++j) g[j] += (double)a[j];
             }
             for (int j = 0; j < W; ++j) {
-                double dact = (M->act == ORACLE_ACT_RELU) ? (u[j] > 0.0 ? 1.0 : 0.0)
-                                                         : M->omega0 * cos(M->omega0 * u[j]);
+                double dact;
+                if (M->act == ORACLE_ACT_RELU) dact = u[j] > 0.0 ? 1.0 : 0.0;
+                else if (M->act == ORACLE_ACT_FINER)  /* d/du sin(w0 (|u| + 1) u) */
+                    dact = M->omega0 * (2.0 * fabs(u[j]) + 1.0) * cos(M->omega0 * (fabs(u[j]) + 1.0) * u[j]);
+                else dact = M->omega0 * cos(M->omega0 * u[j]);
                 g[j] *= dact;               /* now d y / d u_l */
             }
             const int fan = (l == 1) ? D : W;

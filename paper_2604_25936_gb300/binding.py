@@ -22,7 +22,7 @@ _STATUS = {0: "SAND_OK", 1: "SAND_EINVAL", 2: "SAND_ENOMEM", 3: "SAND_EFORMAT", 
            5: "SAND_ETIMEOUT", 6: "SAND_ENOMAP", 7: "SAND_EUNSUPPORTED"}
 PRECISION = {"fp32": 0, "fp32_simt": 1, "fp16": 2, "bf16": 3, "fp8": 4}
 TAIL_LINEAR, TAIL_MULT = 0, 1
-ACT_SINE, ACT_RELU = 0, 1
+ACT_SINE, ACT_RELU, ACT_FINER = 0, 1, 2
 ENC_NONE, ENC_FOURIER = 0, 1
 FLAG_NAN_INPUT, FLAG_TIMEOUT = 1, 2
 
@@ -82,7 +82,8 @@ EXPORTS = ("sand_load_tmlp", "sand_load_tmlp_mem", "sand_load_depth_map", "sand_
            "sand_workspace_bytes", "sand_query_sdf", "sand_query_sdf_grad", "sand_query_sdf_host",
            "sand_read_stats", "sand_model_desc", "sand_free", "sand_last_error", "sand_server_create",
            "sand_server_submit", "sand_server_wait", "sand_server_stats", "sand_server_destroy",
-           "sand_trace_state_bytes", "sand_sphere_trace", "sand_build_depth_map", "sand_query_sdf_dynamic")
+           "sand_trace_state_bytes", "sand_sphere_trace", "sand_build_depth_map", "sand_query_sdf_dynamic",
+           "sand_probe_rate")
 
 
 def lib() -> ctypes.CDLL:
@@ -119,11 +120,25 @@ def lib() -> ctypes.CDLL:
                                     P, P]
     L.sand_build_depth_map.argtypes = [P, ctypes.POINTER(DepthMapDesc), P, P, ctypes.POINTER(MapBuildOpts), P, P]
     L.sand_query_sdf_dynamic.argtypes = [P, P, I64, ctypes.c_float, P, P, ctypes.POINTER(QueryOpts), P]
+    L.sand_probe_rate.argtypes = [I32, I32, I32, I32, P, P]
     for name in EXPORTS:
         if name not in ("sand_workspace_bytes", "sand_last_error", "sand_trace_state_bytes"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
+
+
+PROBE_FFMA, PROBE_SIN = 0, 1
+PROBE_THREADS, PROBE_CHAINS = 256, 8
+
+
+def probe_rate(kind: int, n_blocks: int, iters: int, sink: torch.Tensor, stream: Optional[torch.cuda.Stream] = None):
+    """Launch an issue-rate probe (sand_probe_rate) on sink's device: PROBE_FFMA runs
+    2 * PROBE_CHAINS * iters * PROBE_THREADS * n_blocks FLOP, PROBE_SIN
+    PROBE_CHAINS * iters * PROBE_THREADS * n_blocks hardware sines.  Time it with events."""
+    assert sink.is_cuda and sink.dtype == torch.float32 and sink.numel() >= n_blocks * PROBE_THREADS
+    _check(lib().sand_probe_rate(int(kind), sink.device.index, int(n_blocks), int(iters),
+                                 ctypes.c_void_p(sink.data_ptr()), _stream_handle(stream)))
 
 
 def _check(status: int):

@@ -71,7 +71,7 @@ static sand_status validate_desc(const sand_tmlp_desc &d) {
     if (d.n_layers < 1 || d.n_layers > kMaxLayers) { set_error("n_layers %d outside 1..%d", d.n_layers, kMaxLayers); return SAND_EFORMAT; }
     if (d.width < 1 || d.width > kMaxWidth) { set_error("width %d outside 1..%d", d.width, kMaxWidth); return SAND_EFORMAT; }
     if (d.tail_kind != SAND_TAIL_LINEAR && d.tail_kind != SAND_TAIL_MULT) { set_error("bad tail_kind %d", d.tail_kind); return SAND_EFORMAT; }
-    if (d.activation != SAND_ACT_SINE && d.activation != SAND_ACT_RELU) { set_error("bad activation %d", d.activation); return SAND_EFORMAT; }
+    if (d.activation != SAND_ACT_SINE && d.activation != SAND_ACT_RELU && d.activation != SAND_ACT_FINER) { set_error("bad activation %d", d.activation); return SAND_EFORMAT; }
     if (d.encoder == SAND_ENC_FOURIER) {
         if (d.n_freq < 1 || d.in_dim != 2 * d.n_freq || d.in_dim > kMaxWidth) { set_error("Fourier encoder needs in_dim = 2 n_freq <= %d", kMaxWidth); return SAND_EFORMAT; }
     } else if (d.encoder == SAND_ENC_NONE) {

@@ -1,4 +1,4 @@
-// One instantiation of the tensor-core T-MLP kernel per activation and tail kind, for the
+// One instantiation of the tensor-core T-MLP kernel per activation (SIREN, ReLU, FINER) and tail kind, for the
 // precision mode SAND_INST_MODE and the kernel variant SAND_INST_VAR (0 plain, 1 extended
 // outputs, 2 gradient), set by the including translation unit.
 #include "tc_kernel.cuh"
@@ -25,6 +25,10 @@ cudaError_t launch_tc_mode<SAND_INST_MODE, SAND_INST_VAR>(const CUtensorMap &map
         return tail == SAND_TAIL_MULT
                    ? launch_one<SAND_ACT_RELU, SAND_TAIL_MULT>(map, P, pts, sorted, hdr, n, full_depth, out, grid, smem, s)
                    : launch_one<SAND_ACT_RELU, SAND_TAIL_LINEAR>(map, P, pts, sorted, hdr, n, full_depth, out, grid, smem, s);
+    if (act == SAND_ACT_FINER)
+        return tail == SAND_TAIL_MULT
+                   ? launch_one<SAND_ACT_FINER, SAND_TAIL_MULT>(map, P, pts, sorted, hdr, n, full_depth, out, grid, smem, s)
+                   : launch_one<SAND_ACT_FINER, SAND_TAIL_LINEAR>(map, P, pts, sorted, hdr, n, full_depth, out, grid, smem, s);
     return tail == SAND_TAIL_MULT
                ? launch_one<SAND_ACT_SINE, SAND_TAIL_MULT>(map, P, pts, sorted, hdr, n, full_depth, out, grid, smem, s)
                : launch_one<SAND_ACT_SINE, SAND_TAIL_LINEAR>(map, P, pts, sorted, hdr, n, full_depth, out, grid, smem, s);

@@ -90,6 +90,7 @@ struct TcParams {
                               // tail |t_l| < dyn_r; a tile stops issuing MMAs once all its rows have stopped
     uint8_t *exit_out;        // dynamic exit: the layer each row stopped at (optional)
     float *grad;              // gradient variant: dy/dx per point, [n][3]
+    float finer_k;            // FINER: 1 / omega0 (the activation of phase u = omega0 z is sin(u + u |u| / omega0))
     int kpad;                 // padded K of the packed weight matrix (multiple of 64; of 128 in the FP8 mode)
     int n_stages;
     uint32_t stage_bytes;     // parts x W x 128: one K-block of the weights (hi and lo in the float32 mode)
@@ -301,9 +302,13 @@ __device__ __forceinline__ int tc_row_depth(const WsHeader *hdr, uint32_t r, int
     return d;
 }
 
+// FINER's sin(omega0 (|z| + 1) z) in terms of the phase u = omega0 z: sin(u + u |u| k), k = 1 / omega0
+__device__ __forceinline__ float finer_phase(float u, float k) { return fmaf(u * fabsf(u), k, u); }
+
 template <int ACT>
-__device__ __forceinline__ float activate(float t) {
+__device__ __forceinline__ float activate(float t, float fk) {
     if (ACT == SAND_ACT_RELU) return fmaxf(t, 0.f);
+    if (ACT == SAND_ACT_FINER) return __sinf(finer_phase(t, fk));
     return __sinf(t);
 }
 
@@ -352,10 +357,11 @@ __device__ __forceinline__ void tmem_st_half(uint32_t taddr, const uint32_t *v) 
 // GRAD: the four rows of a point (lanes 4p .. 4p+3 of a warp) carry its value (is_val) and the
 // derivatives along x, y, z of every activation (forward-mode tangents): a tangent row's
 // pre-activation is the derivative of the value row's, without the bias; its activation is
-// cos(u) du (sine, one hardware sine of u + pi/2 for the point's u) or [u > 0] du (ReLU).
+// cos(u) du (sine, one hardware sine of u + pi/2 for the point's u) or [u > 0] du (ReLU);
+// FINER: cos(p) (1 + 2 |u| k) du with p = u + u |u| k its phase.
 template <int MODE, int ACT, int TAIL, bool GRAD = false>
 __device__ __forceinline__ void epilogue16(const float *cs, int W, float c1, const uint32_t *v, int c0, bool write_a,
-                                           uint32_t a_hi, uint32_t a_lo, float &sa, float &sb, bool is_val = true) {
+                                           uint32_t a_hi, uint32_t a_lo, float &sa, float &sb, bool is_val, float fk) {
     constexpr bool MULT = TAIL == SAND_TAIL_MULT;
     uint32_t phi[8], plo[8], p8[4];
 #pragma unroll
@@ -379,12 +385,16 @@ __device__ __forceinline__ void epilogue16(const float *cs, int W, float c1, con
         for (int i = 0; i < 8; ++i) {
             float hv;
             if (!GRAD) {
-                hv = activate<ACT>(fmaf(__uint_as_float(v[8 * g + i]), c1, bv[i]));
+                hv = activate<ACT>(fmaf(__uint_as_float(v[8 * g + i]), c1, bv[i]), fk);
             } else {
                 const float u = fmaf(__uint_as_float(v[8 * g + i]), c1, is_val ? bv[i] : 0.f);
                 const float uv = __shfl_sync(0xffffffffu, u, (threadIdx.x & 31) & ~3);  // the point's u
                 if (ACT == SAND_ACT_RELU) {
                     hv = is_val ? fmaxf(u, 0.f) : (uv > 0.f ? u : 0.f);
+                } else if (ACT == SAND_ACT_FINER) {
+                    const float pv = finer_phase(uv, fk);  // the point's phase
+                    const float sv = __sinf(is_val ? pv : pv + 1.57079632679489662f);
+                    hv = is_val ? sv : sv * (u * fmaf(2.f * fabsf(uv), fk, 1.f));
                 } else {
                     const float sv = __sinf(is_val ? u : uv + 1.57079632679489662f);
                     hv = is_val ? sv : sv * u;
@@ -830,7 +840,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                             uint32_t v[16];
                             tmem_ld16(t_lane + (uint32_t)c0, v);
                             tmem_wait_ld();
-                            epilogue16<MODE, ACT, TAIL, GRAD>(cs, W, c1, v, c0, !last, a_hi_l, a_lo_l, sa, sb, is_val);
+                            epilogue16<MODE, ACT, TAIL, GRAD>(cs, W, c1, v, c0, !last, a_hi_l, a_lo_l, sa, sb, is_val, P.finer_k);
                         }
                         if (!last && !dyn) signal(&a_ready[kb], true);
                     }
@@ -844,17 +854,17 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
 #pragma unroll
                     for (int kb = 1; kb < 4; ++kb)
                         if (kb < KB) tmem_ld32(t_lane + (uint32_t)(64 * kb + su0), v[kb]);
-                    epilogue16<MODE, ACT, TAIL, GRAD>(cs, W, c1, v[0], su0, !last, a_hi_l, a_lo_l, sa, sb, is_val);
-                    epilogue16<MODE, ACT, TAIL, GRAD>(cs, W, c1, v[0] + 16, su0 + 16, !last, a_hi_l, a_lo_l, sa, sb, is_val);
+                    epilogue16<MODE, ACT, TAIL, GRAD>(cs, W, c1, v[0], su0, !last, a_hi_l, a_lo_l, sa, sb, is_val, P.finer_k);
+                    epilogue16<MODE, ACT, TAIL, GRAD>(cs, W, c1, v[0] + 16, su0 + 16, !last, a_hi_l, a_lo_l, sa, sb, is_val, P.finer_k);
                     tmem_wait_ld();
                     signal(d_drained, false);  // the next layer may overwrite the accumulator
                     if (!last && !dyn) signal(&a_ready[0], true);
 #pragma unroll
                     for (int kb = 1; kb < 4; ++kb) {
                         if (kb < KB) {
-                            epilogue16<MODE, ACT, TAIL, GRAD>(cs, W, c1, v[kb], 64 * kb + su0, !last, a_hi_l, a_lo_l, sa, sb, is_val);
+                            epilogue16<MODE, ACT, TAIL, GRAD>(cs, W, c1, v[kb], 64 * kb + su0, !last, a_hi_l, a_lo_l, sa, sb, is_val, P.finer_k);
                             epilogue16<MODE, ACT, TAIL, GRAD>(cs, W, c1, v[kb] + 16, 64 * kb + su0 + 16, !last, a_hi_l,
-                                                              a_lo_l, sa, sb, is_val);
+                                                              a_lo_l, sa, sb, is_val, P.finer_k);
                             if (!last && !dyn) signal(&a_ready[kb], true);
                         }
                     }

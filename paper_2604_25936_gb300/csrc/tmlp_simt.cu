@@ -133,6 +133,12 @@ tmlp_simt_kernel(TmlpDev M, const float *__restrict__ pts, const float4 *__restr
                         if (M.act == SAND_ACT_RELU) {
                             hv = u > 0.f ? u : 0.f;
                             dact = u > 0.f ? 1.f : 0.f;
+                        } else if (M.act == SAND_ACT_FINER) {  // sin(w0 (|u| + 1) u), slope w0 (2 |u| + 1) cos
+                            const float au = fabsf(u);
+                            float sv, cv;
+                            sincosf(M.omega0 * fmaf(au, u, u), &sv, &cv);
+                            hv = sv;
+                            dact = M.omega0 * fmaf(2.f, au, 1.f) * cv;
                         } else {
                             float sv, cv;
                             sincosf(M.omega0 * u, &sv, &cv);

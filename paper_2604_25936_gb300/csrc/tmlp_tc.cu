@@ -30,7 +30,7 @@ bool tc_supported(const sand_tmlp_desc &d, int precision) {
     if (d.width == 336 && mode_of(precision) == TC_SPLIT16) return false;
     if (d.encoder == SAND_ENC_FOURIER && d.in_dim != d.width) return false;
     // FP8 stores the activations unscaled, which holds for the sine's [-1, 1] only
-    if (mode_of(precision) == TC_FP8 && d.activation != SAND_ACT_SINE) return false;
+    if (mode_of(precision) == TC_FP8 && d.activation == SAND_ACT_RELU) return false;  // |h| <= 1 only for sines
     return d.n_layers >= 1;
 }
 
@@ -67,7 +67,7 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
     if (tc->packed_precision == precision && tc->d_pack) return SAND_OK;
     tc_release(tc);
     const int L = d.n_layers, W = d.width, D = d.in_dim, mf = d.n_freq;
-    const bool sine = d.activation == SAND_ACT_SINE;
+    const bool sine = d.activation != SAND_ACT_RELU;  // SIREN or FINER: phase in radians
     // Layer 1 always runs on the tensor cores.  Fourier features feed it as a W-wide A
     // operand; raw coordinates feed one K = 16 MMA whose K slots hold the cross terms of a
     // three-part fp16 split of 256 x (exact for float32 x) and a two-part split of the
@@ -224,6 +224,7 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
     TcParams &P = pk->P;
     P.L = L; P.W = W; P.D = fold1 ? 16 : D; P.l1_fold = fold1 ? 1 : 0; P.x_scale = x_scale; P.tail_kind = d.tail_kind; P.act = d.activation; P.enc = d.encoder; P.m = mf;
     P.first_mma = first;
+    P.finer_k = d.activation == SAND_ACT_FINER ? (float)(1.0 / (double)d.omega0) : 0.f;
     P.kpad = kpad;
     P.stage_bytes = 2u * (uint32_t)W * 128u;  // hi and lo of one K-block, or two K-blocks of the one-part modes
     P.box_rows = box_rows;

@@ -34,7 +34,7 @@ from typing import Callable, Optional
 import numpy as np
 
 TAIL_LINEAR, TAIL_MULT = 0, 1
-ACT_SINE, ACT_RELU = 0, 1
+ACT_SINE, ACT_RELU, ACT_FINER = 0, 1, 2
 ENC_NONE, ENC_FOURIER = 0, 1
 
 MODEL_MAGIC = b"TMLP"
@@ -121,6 +121,17 @@ def siren_tmlp(n_layers: int, width: int, seed: int, tail_kind: int = TAIL_LINEA
         tw[0, 1, :] = 0.0
     return TMLP(L, W, 3, tail_kind, ACT_SINE, ENC_NONE, 0, float(omega0), None,
                 _f32(W1), _f32(b1), _f32(Wh), _f32(bh), _f32(tw), _f32(tb))
+
+
+def finer_tmlp(n_layers: int, width: int, seed: int, tail_kind: int = TAIL_LINEAR, omega0: float = 30.0,
+               bias_k: float = 1.0) -> TMLP:
+    """Random FINER T-MLP: the SIREN-initialised weights of siren_tmlp(n_layers, width, seed,
+    tail_kind, omega0) with the variable-periodic activation sin(omega0 (|z| + 1) z) and the
+    first layer's biases redrawn from U(-bias_k, bias_k) (FINER widens that range to reach
+    the higher-frequency parts of the activation) from PCG64(seed + 7919) in float64."""
+    t = siren_tmlp(n_layers, width, seed, tail_kind=tail_kind, omega0=omega0)
+    g = np.random.Generator(np.random.PCG64(seed + 7919))
+    return dataclasses.replace(t, activation=ACT_FINER, b1=_f32(g.uniform(-bias_k, bias_k, width)))
 
 
 def relu_ff_tmlp(n_layers: int, width: int, n_freq: int, sigma: float, seed: int,

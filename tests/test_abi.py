@@ -98,6 +98,13 @@ def test_host_side_validation(L, tmp_path):
     st = b.QueryStats()
     assert L.sand_read_stats(None, None, ctypes.byref(st), None) == b.SAND_EINVAL
     assert L.sand_workspace_bytes(None, 1000, 0) >= 1000 * 17
+    # issue-rate probes: argument errors before any device call
+    sink = ctypes.c_void_p(256)
+    assert L.sand_probe_rate(7, 0, 1, 1, sink, None) == b.SAND_EINVAL
+    assert L.sand_probe_rate(b.PROBE_FFMA, 0, 0, 1, sink, None) == b.SAND_EINVAL
+    assert L.sand_probe_rate(b.PROBE_SIN, 0, 1, 0, sink, None) == b.SAND_EINVAL
+    assert L.sand_probe_rate(b.PROBE_SIN, 0, 1, 1, None, None) == b.SAND_EINVAL
+    assert L.sand_probe_rate(b.PROBE_SIN, 0, 1, 1, ctypes.c_void_p(258), None) == b.SAND_EINVAL
 
 
 def test_file_formats_round_trip(tmp_path):
