@@ -75,9 +75,12 @@ struct TcRow {
     int d;
     int64_t idx;
 };
-// bytes after the weight stages and constants: barriers, TMEM slot + abort flag,
-// tail exchange ((kSlices - 1) slices x 2 values x 128 rows)
-constexpr int kMiscBytes = kNumBars * 8 + 16 + (kSlices - 1) * 2 * 128 * 4;
+// bytes after the weight stages and constants: barriers, TMEM slot + abort flag, the tail
+// exchange ((kSlices - 1) slices x 2 values x 128 rows), 16 bytes of alignment slack and two
+// buffers of one 16-byte point row per epilogue thread (the next tile's rows are copied in
+// while the current tile runs)
+constexpr int kRowBufBytes = 2 * kEpiThreads * 16;
+constexpr int kMiscBytes = kNumBars * 8 + 16 + (kSlices - 1) * 2 * 128 * 4 + 16 + kRowBufBytes;
 static_assert(kSlices == 2, "the epilogue loads 32 accumulator columns per K-block and thread");
 
 struct TcParams {
@@ -155,6 +158,15 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
         : "memory");
 }
+// Plain asynchronous global -> shared copies (each thread its own bytes; completion per thread).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -456,6 +468,8 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
     volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
     volatile int *skip = reinterpret_cast<volatile int *>(tmem_slot + 2);  // dynamic exit: the tile is done
     float *tailx = reinterpret_cast<float *>(tmem_slot + 4);  // [kSlices - 1][2 values][128 rows]
+    float4 *rowbuf = reinterpret_cast<float4 *>((reinterpret_cast<uintptr_t>(tailx + (kSlices - 1) * 256) + 15) &
+                                                ~uintptr_t(15));  // [2][kEpiThreads]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n_rows = full_depth ? n : (int64_t)hdr->n_active;
@@ -729,18 +743,38 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             const uint32_t z[4] = {0u, 0u, 0u, 0u};
             tmem_st4(a_hi_l + (uint32_t)(W >> 2), z);
         }
-        // this thread's row of tile tt: coordinates, exit layer, original index (-1 for padding)
-        auto load_row = [&](int64_t tt) {
-            TcRow a{0.f, 0.f, 0.f, 0, -1};
-            const int64_t row = GRAD ? tt * PPT + (r >> 2) : tt * kTileM + r;  // GRAD: 4 rows per point
+        // This thread's row of tile tt (coordinates, exit layer, original index; -1 for padding),
+        // copied asynchronously into buffer `buf` of its own 16-byte slot one tile ahead
+        // (prefetch_row) and read from there (take_row).  Each thread copies and reads only its
+        // own slot, and the two buffers alternate, so no other thread's copy is waited for and
+        // no copy lands on a slot whose last read has not been consumed.
+        const int et = threadIdx.x - 64;
+        auto row_of = [&](int64_t tt) -> int64_t { return GRAD ? tt * PPT + (r >> 2) : tt * kTileM + r; };
+        auto prefetch_row = [&](int64_t tt, int buf) {
+            const int64_t row = row_of(tt);
             if (tt < n_tiles && row < n_rows) {
+                const uint32_t dst = smem_u32(rowbuf + buf * kEpiThreads + et);
+                if (full_depth) {  // [n][3] floats, 4-byte aligned
+                    cp_async4(dst, pts + 3 * row);
+                    cp_async4(dst + 4, pts + 3 * row + 1);
+                    cp_async4(dst + 8, pts + 3 * row + 2);
+                } else {
+                    cp_async16(dst, sorted + row);
+                }
+            }
+            cp_async_commit();
+        };
+        auto take_row = [&](int64_t tt, int buf) {
+            cp_async_wait_all();
+            TcRow a{0.f, 0.f, 0.f, 0, -1};
+            const int64_t row = row_of(tt);
+            if (tt < n_tiles && row < n_rows) {
+                const float4 v = rowbuf[buf * kEpiThreads + et];
+                a.x0 = v.x; a.x1 = v.y; a.x2 = v.z;
                 if (full_depth) {
                     a.idx = row;
                     a.d = L;
-                    a.x0 = pts[3 * row]; a.x1 = pts[3 * row + 1]; a.x2 = pts[3 * row + 2];
                 } else {
-                    const float4 v = sorted[row];
-                    a.x0 = v.x; a.x1 = v.y; a.x2 = v.z;
                     a.idx = __float_as_int(v.w);
                     a.d = tc_row_depth(hdr, (uint32_t)row, L);
                 }
@@ -778,27 +812,33 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             }
             signal(&a_ready[0], true);
         };
-        for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        const int comp = GRAD ? (r & 3) : 0;  // GRAD: 0 = value row, 1..3 = d/dx, d/dy, d/dz row
+        const bool is_val = comp == 0;
+        // the layer-1 A operand of a row: its coordinates, or (tangent rows) a unit vector; one
+        // call for the whole warp (put_a1 holds warp-collective TMEM stores), the row per lane
+        auto put_a1_row = [&](const TcRow &row) {
+            TcRow a1 = row;
+            if (GRAD && !is_val) {
+                a1.x0 = comp == 1 ? 1.f : 0.f;
+                a1.x1 = comp == 2 ? 1.f : 0.f;
+                a1.x2 = comp == 3 ? 1.f : 0.f;
+            }
+            put_a1(a1);
+        };
+        int buf = 0;
+        prefetch_row(blockIdx.x, 0);
+        for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, buf ^= 1) {
             const int Dt = tile_depth(t);
-            const TcRow cur = load_row(t);
+            const TcRow cur = take_row(t, buf);
+            prefetch_row(t + gridDim.x, buf ^ 1);  // the next tile's rows, in flight during this tile
             const int d = cur.d;
             const int64_t idx = cur.idx;
             const float x0 = cur.x0, x1 = cur.x1, x2 = cur.x2;
             float y = 0.f;
             bool alive = idx >= 0;  // dynamic exit: this row still runs
             // ---- the A operand of layer 1: split coordinates, or the Fourier features
-            const int comp = GRAD ? (r & 3) : 0;  // GRAD: 0 = value row, 1..3 = d/dx, d/dy, d/dz row
-            const bool is_val = comp == 0;
             if (P.l1_fold) {
-                // the tangent of the input is a unit vector; one call for the whole warp (put_a1
-                // holds warp-collective TMEM stores), the row selected per lane
-                TcRow a1 = cur;
-                if (GRAD && !is_val) {
-                    a1.x0 = comp == 1 ? 1.f : 0.f;
-                    a1.x1 = comp == 2 ? 1.f : 0.f;
-                    a1.x2 = comp == 3 ? 1.f : 0.f;
-                }
-                put_a1(a1);
+                put_a1_row(cur);
             } else {
                 // Fourier features gamma(x) = [sin 2 pi s, cos 2 pi s]; in_dim == W, same slices as the layers
                 for (int kb = 0; kb < KB; ++kb) {
