@@ -336,8 +336,17 @@ __device__ __forceinline__ void pack2(float a, float b, uint32_t &hi, uint32_t &
         __half2 v = __floats2half2_rn(a, b);
         hi = *reinterpret_cast<uint32_t *>(&v);
         if (MODE == TC_SPLIT16) {
-            const float2 back = __half22float2(v);
-            __half2 l = __floats2half2_rn(a - back.x, b - back.y);
+            // residuals h - fp16(h), exact in float32: one mixed-precision FMA each,
+            // fp16(h) * -1 + h, straight from the packed pair
+            float ra, rb;
+            asm("{\n\t.reg .b16 h0, h1, m1;\n\t"
+                "mov.b32 {h0, h1}, %2;\n\t"
+                "mov.b16 m1, 0xBC00;\n\t"
+                "fma.rn.f32.f16 %0, h0, m1, %3;\n\t"
+                "fma.rn.f32.f16 %1, h1, m1, %4;\n\t}"
+                : "=f"(ra), "=f"(rb)
+                : "r"(hi), "f"(a), "f"(b));
+            __half2 l = __floats2half2_rn(ra, rb);
             lo = *reinterpret_cast<uint32_t *>(&l);
         } else {
             lo = 0;
