@@ -12,7 +12,7 @@ static cudaError_t launch_one(const CUtensorMap &map, const TcParams &P, const f
     auto kern = tmlp_tc_kernel<SAND_INST_MODE, ACT, TAIL, SAND_INST_VAR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, kTcThreads, smem, s>>>(map, P, pts, sorted, hdr, n, full_depth, out);
+    kern<<<grid, tc_threads(SAND_INST_MODE), smem, s>>>(map, P, pts, sorted, hdr, n, full_depth, out);
     return cudaGetLastError();
 }
 

@@ -61,7 +61,12 @@ enum TcMode { TC_SPLIT16 = 0, TC_F16 = 1, TC_BF16 = 2, TC_FP8 = 3 };
 constexpr int kSlices = 2;                  // epilogue warps per TMEM lane quadrant
 constexpr int kSliceUnits = 64 / kSlices;   // units of every 64-unit K-block per epilogue thread
 constexpr int kEpiWarps = 4 * kSlices;
-constexpr int kTcThreads = 64 + 32 * kEpiWarps;
+// The float32 mode adds two warps for the exit-layer-1 rows of a SAND query (on the CUDA
+// cores; SM sub-partitions 2 and 3), which run in the slack of its long MMA phases; 384 x 168
+// registers still fit one SM.  In the one-part modes the MMA phases are 3x shorter and the
+// epilogue has no such slack, so those rows stay on the tensor cores there.
+constexpr int kCcWarps = 2;
+constexpr int tc_threads(int mode) { return 64 + 32 * (kEpiWarps + (mode == TC_SPLIT16 ? kCcWarps : 0)); }
 constexpr int kTileM = 128;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
@@ -104,6 +109,9 @@ struct TcParams {
     const float *cvec;        // [L][3][W]: bias' (w0 b for sine, b for ReLU), tail a, tail b
     const float *B;           // [m][3] Fourier matrix
     const float *tb;          // [L][2] tail biases
+    const float4 *w1p;        // [W]: s (W1[j][0], W1[j][1], W1[j][2], b1[j]) of a raw-coordinate layer 1,
+                              // s = omega0 for the sine families (the phase in radians), 1 for ReLU
+    int cc;                   // exit-layer-1 rows of a SAND query run on the CUDA-core warps (raw coordinates)
 };
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -444,7 +452,7 @@ __device__ __forceinline__ void epilogue16(const float *cs, int W, float c1, con
 }
 
 template <int MODE, int ACT, int TAIL, int VAR>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(tc_threads(MODE), 1)
 tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const float *__restrict__ pts,
                const float4 *__restrict__ sorted, WsHeader *hdr, int64_t n, int full_depth, float *__restrict__ out) {
     constexpr int PARTS = MODE == TC_SPLIT16 ? 2 : 1;
@@ -482,7 +490,14 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n_rows = full_depth ? n : (int64_t)hdr->n_active;
-    const int64_t n_tiles = (n_rows + PPT - 1) / PPT;
+    // A SAND query's rows are sorted by descending exit layer.  With raw coordinates, the rows of
+    // exit layer 1 (bin_start[1] .. n_rows) need only layer 1 and its tail, and two warps of
+    // their own compute them on the CUDA cores (W1 x + b1, the activation, the tail) while the
+    // tensor-core pipeline runs the deeper rows.  Every exit-layer-1 row takes that path,
+    // wherever it falls, so a row's result does not depend on the other rows of the query.
+    const bool cc_on = MODE == TC_SPLIT16 && !EXT && !GRAD && !full_depth && P.cc;
+    const int64_t n_tc_rows = cc_on ? (int64_t)hdr->bin_start[1] : n_rows;  // tensor-core rows
+    const int64_t n_tiles = (n_tc_rows + PPT - 1) / PPT;
     auto tile_depth = [&](int64_t t) -> int { return full_depth ? L : tc_row_depth(hdr, (uint32_t)(t * PPT), L); };
 
     if (threadIdx.x == 0) {
@@ -506,7 +521,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (warp >= 2) {  // constants of every layer, resident for the whole kernel
+    if (warp >= 2 && warp < 2 + kEpiWarps) {  // constants of every layer, resident for the whole kernel
         for (int i = threadIdx.x - 64; i < 3 * L * W; i += kEpiThreads) c_all[i] = __ldg(P.cvec + i);
     }
     tc_fence_before();
@@ -692,7 +707,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             }
         }
         __syncwarp();
-    } else {
+    } else if (warp < 2 + kEpiWarps) {
         // ------------------------------------------------ epilogue warps 2..9
         const int q = warp & 3;                 // TMEM lane quadrant
         const int slice = (warp - 2) >> 2;      // which half of every K-block
@@ -761,7 +776,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
         auto row_of = [&](int64_t tt) -> int64_t { return GRAD ? tt * PPT + (r >> 2) : tt * kTileM + r; };
         auto prefetch_row = [&](int64_t tt, int buf) {
             const int64_t row = row_of(tt);
-            if (tt < n_tiles && row < n_rows) {
+            if (tt < n_tiles && row < n_tc_rows) {
                 const uint32_t dst = smem_u32(rowbuf + buf * kEpiThreads + et);
                 if (full_depth) {  // [n][3] floats, 4-byte aligned
                     cp_async4(dst, pts + 3 * row);
@@ -777,7 +792,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             cp_async_wait_all();
             TcRow a{0.f, 0.f, 0.f, 0, -1};
             const int64_t row = row_of(tt);
-            if (tt < n_tiles && row < n_rows) {
+            if (tt < n_tiles && row < n_tc_rows) {
                 const float4 v = rowbuf[buf * kEpiThreads + et];
                 a.x0 = v.x; a.x1 = v.y; a.x2 = v.z;
                 if (full_depth) {
@@ -963,6 +978,51 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                     }
                 }
             }
+        }
+    } else if (MODE == TC_SPLIT16 && cc_on) {
+        // ------------------------------------------------ CUDA-core warps: exit-layer-1 rows
+        // Each thread takes eight rows at a time (r + 64 k of a 512-row step; steps strided over
+        // the CTAs), sharing every weight load between them, so that eight independent chains
+        // cover the latency of the load, the sine and the tail FMA: the phase
+        // W1' x + b1' of every unit (omega0 folded into W1', b1'), the activation, and tail 1
+        // (affine for both tail kinds).  The next step's rows load meanwhile.
+        constexpr int kCcRows = 8, kCcStep = 32 * kCcWarps * kCcRows;
+        const int ct = threadIdx.x - (64 + kEpiThreads);
+        const int64_t n_cc = n_rows - n_tc_rows;
+        const int64_t stride = (int64_t)gridDim.x * kCcStep;
+        const float *ta = c_all + W;  // layer 1's tail weights
+        const float tb0 = __ldg(P.tb);
+        auto load4 = [&](int64_t base, float4 *v) {
+#pragma unroll
+            for (int k = 0; k < kCcRows; ++k) {
+                const int64_t i = base + 32 * kCcWarps * k;
+                v[k] = i < n_cc ? sorted[n_tc_rows + i] : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+            }
+        };
+        int64_t base = (int64_t)blockIdx.x * kCcStep + ct;
+        float4 v[kCcRows];
+        load4(base, v);
+        while (base < n_cc) {
+            float4 vn[kCcRows];
+            load4(base + stride, vn);
+            float s[kCcRows];
+#pragma unroll
+            for (int k = 0; k < kCcRows; ++k) s[k] = 0.f;
+#pragma unroll 4
+            for (int j = 0; j < W; ++j) {
+                const float4 w = __ldg(P.w1p + j);  // the same unit in every lane: one broadcast
+                const float a = ta[j];
+#pragma unroll
+                for (int k = 0; k < kCcRows; ++k)
+                    s[k] = fmaf(a, activate<ACT>(fmaf(w.x, v[k].x, fmaf(w.y, v[k].y, fmaf(w.z, v[k].z, w.w))), P.finer_k), s[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < kCcRows; ++k) {
+                const int idx = __float_as_int(v[k].w);
+                if (idx >= 0) out[idx] = s[k] + tb0;
+                v[k] = vn[k];
+            }
+            base += stride;
         }
     }
     tc_fence_before();

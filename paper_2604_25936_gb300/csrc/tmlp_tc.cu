@@ -177,8 +177,19 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
     const size_t off_c = (packed.size() + 255) / 256 * 256;
     const size_t off_tb = off_c + cvec.size() * 4;
     const size_t off_B = off_tb + tbv.size() * 4;
-    const size_t total = off_B + (size_t)mf * 3 * 4 + 16;
+    // layer 1 of raw coordinates for the CUDA-core path of exit-layer-1 rows: omega0 (sine
+    // families; 1 for ReLU) times (W1[j][0..2], b1[j]), each product rounded once to float32
+    const size_t off_w1 = (off_B + (size_t)mf * 3 * 4 + 15) / 16 * 16;
+    const size_t total = off_w1 + (size_t)W * 16 + 16;
     std::vector<uint8_t> blob(total, 0);
+    if (fold1) {
+        std::vector<float> w1p((size_t)W * 4);
+        for (int j = 0; j < W; ++j) {
+            for (int c = 0; c < 3; ++c) w1p[(size_t)j * 4 + c] = (float)(turn * (double)W1[(size_t)j * D + c]);
+            w1p[(size_t)j * 4 + 3] = (float)(turn * (double)b1[j]);
+        }
+        memcpy(blob.data() + off_w1, w1p.data(), w1p.size() * 4);
+    }
     memcpy(blob.data(), packed.data(), packed.size());
     memcpy(blob.data() + off_c, cvec.data(), cvec.size() * 4);
     memcpy(blob.data() + off_tb, tbv.data(), tbv.size() * 4);
@@ -239,6 +250,8 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
     P.cvec = reinterpret_cast<const float *>(dbuf + off_c);
     P.tb = reinterpret_cast<const float *>(dbuf + off_tb);
     P.B = B ? reinterpret_cast<const float *>(dbuf + off_B) : nullptr;
+    P.w1p = reinterpret_cast<const float4 *>(dbuf + off_w1);
+    P.cc = fold1 ? 1 : 0;
     P.n_stages = 1;
     const size_t fixed = tc_smem_bytes(P, parts) - P.stage_bytes;
     int stages = (int)((kSmemBudget - (long)fixed) / (long)P.stage_bytes);
