@@ -1,0 +1,5 @@
+// Tensor-core T-MLP kernel instantiations: bf16 operands, SAND queries on raw coordinates with the
+// exit-layer-1 rows on two CUDA-core warps.
+#define SAND_INST_MODE TC_BF16
+#define SAND_INST_VAR 3
+#include "tc_inst_body.cuh"

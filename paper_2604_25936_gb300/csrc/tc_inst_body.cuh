@@ -1,6 +1,6 @@
 // One instantiation of the tensor-core T-MLP kernel per activation (SIREN, ReLU, FINER) and tail kind, for the
 // precision mode SAND_INST_MODE and the kernel variant SAND_INST_VAR (0 plain, 1 extended
-// outputs, 2 gradient), set by the including translation unit.
+// outputs, 2 gradient, 3 SAND query with CUDA-core warps), set by the including translation unit.
 #include "tc_kernel.cuh"
 
 namespace sand {
@@ -12,7 +12,7 @@ static cudaError_t launch_one(const CUtensorMap &map, const TcParams &P, const f
     auto kern = tmlp_tc_kernel<SAND_INST_MODE, ACT, TAIL, SAND_INST_VAR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, tc_threads(SAND_INST_MODE), smem, s>>>(map, P, pts, sorted, hdr, n, full_depth, out);
+    kern<<<grid, tc_threads(SAND_INST_VAR), smem, s>>>(map, P, pts, sorted, hdr, n, full_depth, out);
     return cudaGetLastError();
 }
 

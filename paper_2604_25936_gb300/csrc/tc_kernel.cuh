@@ -61,12 +61,12 @@ enum TcMode { TC_SPLIT16 = 0, TC_F16 = 1, TC_BF16 = 2, TC_FP8 = 3 };
 constexpr int kSlices = 2;                  // epilogue warps per TMEM lane quadrant
 constexpr int kSliceUnits = 64 / kSlices;   // units of every 64-unit K-block per epilogue thread
 constexpr int kEpiWarps = 4 * kSlices;
-// The float32 mode adds two warps for the exit-layer-1 rows of a SAND query (on the CUDA
-// cores; SM sub-partitions 2 and 3), which run in the slack of its long MMA phases; 384 x 168
-// registers still fit one SM.  In the one-part modes the MMA phases are 3x shorter and the
-// epilogue has no such slack, so those rows stay on the tensor cores there.
+// Kernel variant 3 (SAND queries on raw coordinates) adds two warps for the rows of exit layer
+// 1, on the CUDA cores (SM sub-partitions 2 and 3); 384 x 168 registers still fit one SM.  The
+// other variants keep 320 threads: carried in a full-depth kernel, the extra warps' code costs
+// its epilogue registers.
 constexpr int kCcWarps = 2;
-constexpr int tc_threads(int mode) { return 64 + 32 * (kEpiWarps + (mode == TC_SPLIT16 ? kCcWarps : 0)); }
+constexpr int tc_threads(int var) { return 64 + 32 * (kEpiWarps + (var == 3 ? kCcWarps : 0)); }
 constexpr int kTileM = 128;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
@@ -452,13 +452,14 @@ __device__ __forceinline__ void epilogue16(const float *cs, int W, float c1, con
 }
 
 template <int MODE, int ACT, int TAIL, int VAR>
-__global__ void __launch_bounds__(tc_threads(MODE), 1)
+__global__ void __launch_bounds__(tc_threads(VAR), 1)
 tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const float *__restrict__ pts,
                const float4 *__restrict__ sorted, WsHeader *hdr, int64_t n, int full_depth, float *__restrict__ out) {
     constexpr int PARTS = MODE == TC_SPLIT16 ? 2 : 1;
     constexpr bool MULT = TAIL == SAND_TAIL_MULT;
     constexpr bool EXT = VAR == 1;   // extended outputs: all tails, dynamic exit
     constexpr bool GRAD = VAR == 2;  // value and input gradient: 32 points x 4 rows per tile
+    constexpr bool CCW = VAR == 3;   // SAND query with the exit-layer-1 rows on the CUDA-core warps
     constexpr int PPT = GRAD ? kTileM / 4 : kTileM;  // points per tile
     constexpr int UPS = MODE == TC_FP8 ? 128 : 64;  // K-units per weight stage (one 128-byte row per unit)
     constexpr int UPK = MODE == TC_FP8 ? 32 : 16;   // K-units per MMA (32 bytes of every row)
@@ -495,7 +496,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
     // their own compute them on the CUDA cores (W1 x + b1, the activation, the tail) while the
     // tensor-core pipeline runs the deeper rows.  Every exit-layer-1 row takes that path,
     // wherever it falls, so a row's result does not depend on the other rows of the query.
-    const bool cc_on = MODE == TC_SPLIT16 && !EXT && !GRAD && !full_depth && P.cc;
+    const bool cc_on = CCW && !full_depth && P.cc;
     const int64_t n_tc_rows = cc_on ? (int64_t)hdr->bin_start[1] : n_rows;  // tensor-core rows
     const int64_t n_tiles = (n_tc_rows + PPT - 1) / PPT;
     auto tile_depth = [&](int64_t t) -> int { return full_depth ? L : tc_row_depth(hdr, (uint32_t)(t * PPT), L); };
@@ -979,7 +980,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                 }
             }
         }
-    } else if (MODE == TC_SPLIT16 && cc_on) {
+    } else if (CCW && cc_on) {
         // ------------------------------------------------ CUDA-core warps: exit-layer-1 rows
         // Each thread takes eight rows at a time (r + 64 k of a 512-row step; steps strided over
         // the CTAs), sharing every weight load between them, so that eight independent chains
@@ -1034,7 +1035,8 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
 }
 
 // Launch one instantiation (defined in the per-mode translation units).  VAR 0: the plain
-// query; 1: the extended outputs (all tails, dynamic exit); 2: value and input gradient.
+// query; 1: the extended outputs (all tails, dynamic exit); 2: value and input gradient;
+// 3: a SAND query on raw coordinates with its exit-layer-1 rows on the CUDA-core warps.
 // The plain query path carries none of the others' code, which its single MMA-issuing
 // thread would otherwise pay for at every layer.
 template <int MODE, int VAR>

@@ -292,9 +292,10 @@ cudaError_t launch_tmlp_tc(const TcModel &tc, const TmlpDev &M, const float *pts
     const int64_t tiles = (n + ppt - 1) / ppt;
     int grid = num_sms;
     if (tiles < grid) grid = (int)(tiles > 0 ? tiles : 1);
-    const int var = P.grad ? 2 : (P.all_tails || P.dyn_r > 0.f) ? 1 : 0;
+    const int var = P.grad ? 2 : (P.all_tails || P.dyn_r > 0.f) ? 1 : (!full_depth && P.cc) ? 3 : 0;
 #define SAND_LAUNCH(M)                                                                                                  \
-    (var == 2   ? launch_tc_mode<M, 2>(pk->map, P, P.act, P.tail_kind, pts, sorted, hdr, n, full_depth, out, grid, smem, s) \
+    (var == 3   ? launch_tc_mode<M, 3>(pk->map, P, P.act, P.tail_kind, pts, sorted, hdr, n, full_depth, out, grid, smem, s) \
+     : var == 2 ? launch_tc_mode<M, 2>(pk->map, P, P.act, P.tail_kind, pts, sorted, hdr, n, full_depth, out, grid, smem, s) \
      : var == 1 ? launch_tc_mode<M, 1>(pk->map, P, P.act, P.tail_kind, pts, sorted, hdr, n, full_depth, out, grid, smem, s) \
                 : launch_tc_mode<M, 0>(pk->map, P, P.act, P.tail_kind, pts, sorted, hdr, n, full_depth, out, grid, smem, s))
     switch (pk->mode) {
