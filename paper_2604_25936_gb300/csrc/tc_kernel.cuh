@@ -85,7 +85,7 @@ struct TcRow {
 // buffers of one 16-byte point row per epilogue thread (the next tile's rows are copied in
 // while the current tile runs)
 constexpr int kRowBufBytes = 2 * kEpiThreads * 16;
-constexpr int kMiscBytes = kNumBars * 8 + 16 + (kSlices - 1) * 2 * 128 * 4 + 16 + kRowBufBytes;
+constexpr int kMiscBytes = kNumBars * 8 + 16 + (kSlices - 1) * 2 * 128 * 4 + 16 + kRowBufBytes + 16 * 4;
 static_assert(kSlices == 2, "the epilogue loads 32 accumulator columns per K-block and thread");
 
 struct TcParams {
@@ -315,10 +315,12 @@ __device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t *v) {
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // ------------------------------------------------------------------ helpers
-__device__ __forceinline__ int tc_row_depth(const WsHeader *hdr, uint32_t r, int L) {
+// Exit layer of sorted row r: the smallest d with bin_start[d] <= r (bins in descending order),
+// from the CTA's shared copy of bin_start.
+__device__ __forceinline__ int tc_row_depth(const uint32_t *bin_start, uint32_t r, int L) {
     int d = L;
     for (int k = L - 1; k >= 1; --k)
-        if (hdr->bin_start[k] <= r) d = k;
+        if (bin_start[k] <= r) d = k;
     return d;
 }
 
@@ -488,6 +490,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
     float *tailx = reinterpret_cast<float *>(tmem_slot + 4);  // [kSlices - 1][2 values][128 rows]
     float4 *rowbuf = reinterpret_cast<float4 *>((reinterpret_cast<uintptr_t>(tailx + (kSlices - 1) * 256) + 15) &
                                                 ~uintptr_t(15));  // [2][kEpiThreads]
+    uint32_t *s_bin = reinterpret_cast<uint32_t *>(rowbuf + 2 * kEpiThreads);  // [16]: bin_start, read per tile
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n_rows = full_depth ? n : (int64_t)hdr->n_active;
@@ -499,7 +502,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
     const bool cc_on = CCW && !full_depth && P.cc;
     const int64_t n_tc_rows = cc_on ? (int64_t)hdr->bin_start[1] : n_rows;  // tensor-core rows
     const int64_t n_tiles = (n_tc_rows + PPT - 1) / PPT;
-    auto tile_depth = [&](int64_t t) -> int { return full_depth ? L : tc_row_depth(hdr, (uint32_t)(t * PPT), L); };
+    auto tile_depth = [&](int64_t t) -> int { return full_depth ? L : tc_row_depth(s_bin, (uint32_t)(t * PPT), L); };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < P.n_stages; ++s) {
@@ -514,6 +517,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
         mbar_init(smem_u32(x_empty), 128);
         *abort = 0;
         *skip = 0;
+        for (int k = 0; k < 16; ++k) s_bin[k] = hdr->bin_start[k];
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -801,7 +805,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                     a.d = L;
                 } else {
                     a.idx = __float_as_int(v.w);
-                    a.d = tc_row_depth(hdr, (uint32_t)row, L);
+                    a.d = tc_row_depth(s_bin, (uint32_t)row, L);
                 }
             }
             return a;
