@@ -20,8 +20,8 @@ smallest |u| (the oracle's margin) is within the pre-activation error of 0 may t
 ReLU decisions than the oracle.  The comparison holds on the points whose margin exceeds
 1e-4 (float32) or the 16-bit relative bound above times L (16-bit), and at least 30 such
 points must remain.
-The value output of a gradient query must agree with the plain query of the same
-precision to a few float32 ulps: the value row's arithmetic is the same.
+The value outputs of the gradient query and of the plain query (whose layer 1 may run on the
+CUDA cores instead) are both held to the oracle at the precision's value tolerance.
 """
 import numpy as np
 import pytest
@@ -33,6 +33,8 @@ import synth
 pytestmark = pytest.mark.gpu
 
 REL16 = {"fp16": 2.0 ** -10, "bf16": 2.0 ** -7}
+# value tolerances of the parity tests: float32 1e-5, 16-bit 2e-3 (ReLU models in bf16: 2^-8 per layer)
+VTOL = {"fp32": 1e-5, "fp16": 2e-3, "bf16": 2e-3}
 
 
 def load(model, tree=None):
@@ -93,10 +95,13 @@ def test_tc_gradient_parity(kind, prec):
     print("tc-grad %s/%s: %d points, max|g| %.3g  err %.3g  tol %.3g  (%.2e of max|g|)"
           % (kind, prec, keep.sum(), gscale, e, tol, e / gscale))
     assert e <= tol, (kind, prec, e, tol)
-    # the value of the same query without the gradient: the same arithmetic on the value row
+    # values of the gradient query and of the plain query (whose layer 1 may run on the CUDA
+    # cores) against the oracle, at the precision's value tolerance
     y_plain = m.query(dev(pts), precision=prec).double().cpu().numpy()
     vscale = max(1.0, float(np.abs(y_ref).max()))
-    assert err_of(y, y_plain) <= 4 * 2.0 ** -23 * vscale
+    relu_bf16 = model.activation == synth.ACT_RELU and prec == "bf16"
+    vtol = (2.0 ** -8 * model.n_layers if relu_bf16 else VTOL[prec]) * vscale
+    assert err_of(y, y_ref) <= vtol and err_of(y_plain, y_ref) <= vtol, (err_of(y, y_ref), err_of(y_plain, y_ref), vtol)
     m.free()
 
 
