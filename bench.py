@@ -17,6 +17,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import re
 import os
 import statistics
 import subprocess
@@ -107,16 +108,24 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def code_sha1(path: str) -> str:
+    """sha1 of a C/CUDA source with its comments and blank lines removed: a change to the
+    comments alone leaves the kernel, and so the counters taken from it, unchanged."""
+    src = open(path).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in src.splitlines()]
+    return hashlib.sha1("\n".join(ln for ln in lines if ln.strip()).encode()).hexdigest()
+
+
 def kernel_traffic(prec: str):
     """DRAM bytes per launch of the dominant kernel from the committed ncu summary, or None
-    when the kernel source changed since the counters were taken."""
+    when the kernel's code changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     try:
         t = json.load(open(path)).get(KERNEL_NAME[prec] + ":" + prec)
-        src = open(os.path.join(ROOT, KERNEL_SRC[prec]), "rb").read()
-        if t and t.get("source_sha1") == hashlib.sha1(src).hexdigest():
+        if t and t.get("code_sha1") == code_sha1(os.path.join(ROOT, KERNEL_SRC[prec])):
             return t.get("dram_bytes_per_launch_full_workload")
     except Exception:
         return None

@@ -1,7 +1,8 @@
 // Tensor-core T-MLP kernel for sm_103a (tcgen05 MMA, TMEM accumulators, TMA).
 //
 // Evaluates Eq. 2 (and Eq. 3 for multiplicative tails) for 128-row tiles of
-// points sorted by descending exit layer.  One persistent CTA per SM, 320 threads:
+// points sorted by descending exit layer.  One persistent CTA per SM, 320 threads
+// (384 in variant 3):
 //   warp 0       TMA producer: streams weight tiles (64 K-columns x W units, one
 //                K-block of one layer) from L2 into a ring of stages, 128-byte
 //                swizzled (the K-major layout the MMA reads).
@@ -9,15 +10,18 @@
 //                D[128 x W] (fp32, TMEM) += A[128 x 16] . B[W x 16]^T, A read from TMEM.
 //   warps 2..9   epilogue.  Thread (quadrant q, lane i) owns tile row 32 q + i (the
 //                TMEM lane restriction); the two warps of a quadrant take half of the
-//                units of every K-block each.  Layer 1 (float32, on the CUDA cores), bias,
-//                sine, tails, the running sum y_l = y_{l-1} + t_l and the write at
-//                each row's exit layer.  The new activations are packed to fp16 and
-//                written with tcgen05.st into TMEM, where the next layer's MMAs read
-//                them as the A operand.
+//                units of every K-block each.  Layer 1's operand (the split coordinates
+//                of one K = 16 MMA), bias, sine, tails, the running sum
+//                y_l = y_{l-1} + t_l and the write at each row's exit layer.  The new
+//                activations are packed (fp16 pair, bf16 or e4m3) and written with
+//                tcgen05.st into TMEM, where the next layer's MMAs read them as the A
+//                operand.
+//   warps 10,11  (variant 3, SAND queries on raw coordinates) every row of exit layer 1,
+//                entirely on the CUDA cores: layer 1, its sine and tail 1 in float32.
 // TMEM columns: [0, W) accumulator, then A_hi (W/2 columns of packed fp16 pairs)
 // and, in the float32 mode, A_lo.  One MMA stream at N = W: measured on GB300, one
-// issuing thread sustains about one M=128 MMA per 140-165 cycles whatever N is, so
-// N = 256 is what reaches the tensor cores' rate.
+// M=128 N=256 K=16 MMA per 128 cycles when each weight stage's MMAs leave the issuing
+// thread as one asm run, so N = 256 is what reaches the tensor cores' rate.
 // Overlap of a layer's epilogue with the next layer's MMAs: each epilogue thread
 // first loads all of its accumulator columns into registers (128 at W = 256) and
 // signals d_drained (the next layer may now overwrite D), then produces the next A
@@ -25,10 +29,10 @@
 // MMAs of the next layer on K-block kb start as soon as a_ready[kb] completes.
 // Thread (quadrant, slice s) owns units 64 kb + 32 s .. + 31 of every K-block kb.
 // Two epilogue warps per SM sub-partition (not four) leave the MMA-issuing thread
-// issue slots when it is on the critical path, and 200 registers per thread.
+// issue slots when it is on the critical path, and 168 registers per thread.
 // A tile runs to the exit layer of its first (deepest) row; rows whose exit layer
 // was reached ride along only in the one tile per exit layer that straddles two
-// layers; tiles of exit layer 1 never touch the tensor cores.
+// layers; in variant 3 no row of exit layer 1 reaches the tensor cores.
 //
 // Precision modes (hidden-layer products only; everything else is float32):
 //   SPLIT16  a = a_hi + a_lo and w*s = w_hi + w_lo with fp16 terms (s = 2^-e per
