@@ -50,10 +50,10 @@ typedef enum {
 
 /* Arithmetic of the hidden-layer products W_i h_{i-1} (Eq. 2).  The first
  * layer, the sine argument and its range reduction, the tails and the
- * accumulation y_i = y_{i-1} + t_i are always float32.  In a SAND query of a
- * model on raw coordinates, points whose exit layer is 1 are computed entirely
- * in float32 on the CUDA cores whatever the mode, and every such point the same
- * way, so a point's result does not depend on the other points of the call.
+ * accumulation y_i = y_{i-1} + t_i are always float32.  In a SAND query without
+ * gradients of a model on raw coordinates, points whose exit layer is 1 are
+ * computed entirely in float32 on the CUDA cores whatever the mode, every such
+ * point the same way; no point's result depends on the other points of a call.
  *   SAND_FP32       tcgen05 tensor cores, each float32 operand split into two
  *                   fp16 terms (weights pre-scaled by a power of two), three
  *                   products per layer, float32 accumulation: float32-class error.
