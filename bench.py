@@ -47,6 +47,18 @@ KERNEL_NAME = {"fp32_simt": "tmlp_simt_kernel", "fp32": "tmlp_tc_kernel", "fp16"
 METRIC = "SDF queries/s, SAND vs full-depth T-MLP on 1 GB300 at stated error; serve p99 ms"
 
 
+def hbm_stages(n: int, n_far: int, ms: float, peak_gbs: float) -> dict:
+    """Bandwidth of the memory-bound stages of a SAND query (workspace reset, lookup, scan,
+    scatter): the lookup reads a point (12 B) and writes its exit layer (1 B; far points also
+    their stored value, 4 B); the scatter reads both again (13 B) and writes the sorted row
+    (16 B); the per-block histograms are a few KB."""
+    bytes_ = 42 * n + 4 * n_far
+    gbs = bytes_ / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+    return {"kernels": "lookup_kernel + scan_kernel + scatter_kernel", "bytes_per_point": 42,
+            "bytes": bytes_, "ms": ms, "achieved": gbs, "peak": peak_gbs, "unit": "GB/s",
+            "frac": gbs / peak_gbs if peak_gbs else None}
+
+
 def flops_per_point(d: np.ndarray, W: int, tail_mult: bool) -> np.ndarray:
     """Algorithmic FLOPs of a point that exits at layer d >= 1: layer 1 (2*3*W),
     d-1 hidden products (2*W^2 each) and d tails (2*W, or 4*W for multiplicative tails >= 2)."""
@@ -819,6 +831,7 @@ def main():
         "max_abs_err_vs_oracle_20k": err,
         "tolerance": TOL[prec],
         "stage_ms": {"lookup_bin": sum(pre_ms) / K, "tmlp": mlp_avg},
+        "hbm_stages": hbm_stages(n, int(counts[0]), sum(pre_ms) / K, pk.get("hbm_gbs", 6800.0)),
         "exit_layer_histogram": hist,
         "roofline": roof,
         "epilogue_pipe": epi,
