@@ -304,7 +304,8 @@ sand_status sand_server_create(const sand_model *models, int n_models, const san
  * buffers must stay valid until sand_server_wait returns for *ticket. */
 sand_status sand_server_submit(sand_server s, int model, const float *h_points, int64_t n, float *h_out,
                                uint64_t *ticket);
-/* Block until the request completed (SAND_ETIMEOUT after timeout_s seconds);
+/* Block until the request completed (SAND_ETIMEOUT after timeout_s seconds;
+ * SAND_EINVAL for a negative or NaN timeout_s, values above 1e7 s are clamped);
  * *latency_ms (nullable) receives its submit-to-result time. */
 sand_status sand_server_wait(sand_server s, uint64_t ticket, double timeout_s, double *latency_ms);
 /* Latency percentiles and throughput of the requests completed so far. */

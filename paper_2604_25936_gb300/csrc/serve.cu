@@ -369,6 +369,8 @@ sand_status sand_server_submit(sand_server S, int model, const float *h_points, 
 
 sand_status sand_server_wait(sand_server S, uint64_t ticket, double timeout_s, double *latency_ms) {
     if (!S) { set_error("NULL server"); return SAND_EINVAL; }
+    if (!(timeout_s >= 0.0)) { set_error("timeout_s must be a number >= 0"); return SAND_EINVAL; }
+    if (timeout_s > 1e7) timeout_s = 1e7;  // about 116 days: keeps the deadline arithmetic finite
     std::unique_lock<std::mutex> lk(S->mu);
     auto it = S->requests.find(ticket);
     if (it == S->requests.end()) { set_error("unknown ticket %llu", (unsigned long long)ticket); return SAND_EINVAL; }

@@ -1,0 +1,76 @@
+"""Argument errors at the C-ABI boundary, without a GPU.
+
+Every entry point that takes a model, a server or a buffer must refuse a NULL handle or a
+malformed argument with SAND_EINVAL and a message (sand_last_error), before any device
+work, and the calls documented as no-ops on NULL must return SAND_OK.
+"""
+import ctypes
+
+import pytest
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2604_25936_gb300 import binding, build
+    build.build()
+    L = binding.lib()
+    L.sand_query_sdf_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p]
+    L.sand_query_sdf_noalloc.restype = ctypes.c_int
+    return binding
+
+
+def _einval(B, rc):
+    assert rc == B.SAND_EINVAL, rc
+    assert len(B.lib().sand_last_error()) > 0
+
+
+def test_null_model_is_refused_everywhere(B):
+    L = B.lib()
+    P = ctypes.c_void_p
+    buf = P(256)  # never dereferenced: the NULL model is refused first
+    o = B.QueryOpts()
+    _einval(B, L.sand_query_sdf(None, buf, 10, buf, ctypes.byref(o), None))
+    _einval(B, L.sand_query_sdf_grad(None, buf, 10, buf, buf, ctypes.byref(o), None))
+    _einval(B, L.sand_query_sdf_host(None, buf, 10, buf, ctypes.byref(o), None))
+    _einval(B, L.sand_query_sdf_noalloc(None, buf, 10, buf, ctypes.byref(o), None))
+    _einval(B, L.sand_query_sdf_dynamic(None, buf, 10, ctypes.c_float(0.01), buf, None, ctypes.byref(o), None))
+    d = B.TmlpDesc()
+    _einval(B, L.sand_model_desc(None, ctypes.byref(d)))
+    _einval(B, L.sand_load_depth_map(None, b"x.sdmo"))
+    dm = B.DepthMapDesc()
+    _einval(B, L.sand_load_depth_map_mem(None, ctypes.byref(dm), buf, buf, None))
+    st = B.QueryStats()
+    _einval(B, L.sand_read_stats(None, buf, ctypes.byref(st), None))
+    tr = B.TraceOpts(8, 1e-4, 8, 0)
+    _einval(B, L.sand_sphere_trace(None, buf, 0, buf, 10, ctypes.byref(tr), ctypes.byref(o), buf, buf, buf, None, None))
+    mb = B.MapBuildOpts(4, 1.5e-4, 0, 0)
+    _einval(B, L.sand_build_depth_map(None, ctypes.byref(dm), buf, buf, ctypes.byref(mb), buf, None))
+    assert L.sand_free(None) == B.SAND_OK
+
+
+def test_server_handles(B):
+    L = B.lib()
+    h = ctypes.c_void_p()
+    _einval(B, L.sand_server_create(None, 1, None, ctypes.byref(h)))
+    models = (ctypes.c_void_p * 2)(None, None)
+    _einval(B, L.sand_server_create(models, 2, None, ctypes.byref(h)))  # NULL model in the list
+    _einval(B, L.sand_server_create(models, 0, None, ctypes.byref(h)))
+    t = ctypes.c_uint64()
+    _einval(B, L.sand_server_submit(None, 0, None, 0, None, ctypes.byref(t)))
+    _einval(B, L.sand_server_wait(None, 1, 1.0, None))
+    rep = B.ServerReport()
+    _einval(B, L.sand_server_stats(None, ctypes.byref(rep)))
+    assert L.sand_server_destroy(None) == B.SAND_OK
+
+
+def test_sizes_without_a_device(B):
+    L = B.lib()
+    # workspace: a 1 KiB header, per-block histograms, then 17 B per point (exit byte, float4 row)
+    w0 = L.sand_workspace_bytes(None, 0, 0)
+    w1 = L.sand_workspace_bytes(None, 1 << 20, 0)
+    assert w1 - w0 >= 17 * (1 << 20)
+    assert L.sand_workspace_bytes(None, 1 << 20, 1) == w1  # the gradient needs no more
+    # tracer state: grows with the rays, about 60 B per ray
+    s1, s2 = L.sand_trace_state_bytes(1 << 16), L.sand_trace_state_bytes(1 << 17)
+    assert 40 * (1 << 16) <= s2 - s1 <= 200 * (1 << 16)
