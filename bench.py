@@ -45,6 +45,7 @@ KERNEL_SRC = {"fp32_simt": "paper_2604_25936_gb300/csrc/tmlp_simt.cu", "fp32": "
 KERNEL_NAME = {"fp32_simt": "tmlp_simt_kernel", "fp32": "tmlp_tc_kernel", "fp16": "tmlp_tc_kernel",
                "bf16": "tmlp_tc_kernel", "fp8": "tmlp_tc_kernel"}
 METRIC = "SDF queries/s, SAND vs full-depth T-MLP on 1 GB300 at stated error; serve p99 ms"
+WORKLOAD = "SAND-SIREN 8x256 linear tails, level-7 octree, %d^3 lattice" % GRID
 
 
 def hbm_stages(n: int, n_far: int, ms: float, peak_gbs: float) -> dict:
@@ -144,6 +145,22 @@ def kernel_traffic(prec: str):
     return None
 
 
+def host_cpu() -> str:
+    """The host CPU as /proc/cpuinfo names it (model name, or the Arm implementer and part)."""
+    try:
+        fields = {}
+        for ln in open("/proc/cpuinfo"):
+            k, _, v = ln.partition(":")
+            fields.setdefault(k.strip(), v.strip())
+        if fields.get("model name"):
+            return fields["model name"]
+        if fields.get("CPU implementer"):
+            return "Arm implementer %s part %s" % (fields.get("CPU implementer"), fields.get("CPU part", "?"))
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_baseline(model, tree, pts, budget_s: float = 12.0):
     """The FP64 oracle as it stands, on the host cores, over a seeded sample of the lattice."""
     import oracle
@@ -158,6 +175,7 @@ def cpu_baseline(model, tree, pts, budget_s: float = 12.0):
     oracle.query(model, tree, pts[idx])
     dt = time.perf_counter() - t0
     return {"value": k / dt, "unit": "queries/s", "cores": oracle.threads(), "kind": "oracle",
+            "nproc": os.cpu_count(), "cpu": host_cpu(),
             "sample": "%d lattice points drawn with PCG64 seed 11 from the %d^3 lattice, SAND query (lookup + "
                       "T-MLP to each exit layer) in float64, %.1f s" % (k, GRID, dt)}
 
@@ -191,9 +209,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "SAND-SIREN 8x256, level-7 octree, %d^3 lattice" % GRID, "global_batch": len(pts),
-                       "sample_per_step": k},
+            "config": {"workload": WORKLOAD, "global_batch": len(pts), "sample_per_step": k},
             "cpu_baseline": {"value": value, "unit": "queries/s", "cores": oracle.threads(), "kind": "oracle",
+                             "nproc": os.cpu_count(), "cpu": host_cpu(),
                              "sample": "%d lattice points (PCG64 seed 11) per step, float64 SAND query" % k},
             "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -822,7 +840,7 @@ def main():
         "vs_baseline": None,
         "dtype": DTYPE[prec],
         "data": "synthetic: random SIREN-init 8x256 T-MLP (seed 1), analytic-scene level-7 octree, marching-cubes lattice",
-        "config": {"workload": "SAND-SIREN 8x256 linear tails, level-7 octree, %d^3 lattice" % GRID,
+        "config": {"workload": WORKLOAD,
                    "global_batch": world * n, "points_per_gpu": n, "precision": prec,
                    "l2": "inputs larger than L2 (201 MB of points per step), no flush",
                    "parallelism": "replicas (one full lattice per GPU)"},
