@@ -608,7 +608,7 @@ def run_peaks(args):
             sus = _sustained_ms(fn)
             res[name + "_tflops"] = round(flop / (burst / 1e3) / 1e12, 1)
             res[name + "_tflops_sustained"] = round(flop / (sus / 1e3) / 1e12, 1)
-        except Exception as e:  # a library path missing on this build of torch
+        except Exception as e:  # a library path missing in the installed torch
             res[name + "_tflops"] = None
             res[name + "_error"] = str(e)[:200]
     torch.backends.cuda.matmul.allow_tf32 = False
