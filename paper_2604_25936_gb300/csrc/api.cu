@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <string>
+#include <new>
 #include <vector>
 
 #include "internal.cuh"
@@ -260,6 +261,16 @@ sand_status sand_load_tmlp_mem(const sand_tmlp_desc *desc, const float *h_params
     return SAND_OK;
 }
 
+// Bytes from the current position of f to its end (-1 if unknown): a size field read from a
+// file is checked against this before anything is allocated for it.
+static long long bytes_left(FILE *f) {
+    const long at = ftell(f);
+    if (at < 0 || fseek(f, 0, SEEK_END) != 0) return -1;
+    const long end = ftell(f);
+    if (end < 0 || fseek(f, at, SEEK_SET) != 0) return -1;
+    return (long long)end - (long long)at;
+}
+
 sand_status sand_load_tmlp(const char *path, int device, sand_model *out) {
     g_err.clear();
     if (!path || !out) { set_error("NULL argument"); return SAND_EINVAL; }
@@ -272,9 +283,16 @@ sand_status sand_load_tmlp(const char *path, int device, sand_model *out) {
     uint64_t np;
     bool ok = fread(magic, 1, 4, f) == 4 && memcmp(magic, "TMLP", 4) == 0 && fread(&ver, 4, 1, f) == 1 && ver == 1 &&
               fread(h, 4, 7, f) == 7 && fread(&w0, 4, 1, f) == 1 && fread(&np, 8, 1, f) == 1 && np < (1ull << 31);
+    ok = ok && bytes_left(f) >= (long long)np * 4;  // the parameter block is there in full
     std::vector<float> p;
     if (ok) {
-        p.resize(np);
+        try {
+            p.resize(np);
+        } catch (const std::bad_alloc &) {
+            fclose(f);
+            set_error("%s: cannot hold %llu parameters in host memory", path, (unsigned long long)np);
+            return SAND_ENOMEM;
+        }
         ok = fread(p.data(), 4, np, f) == np;
     }
     fclose(f);
@@ -326,14 +344,22 @@ sand_status sand_load_depth_map(sand_model m, const char *path) {
     bool ok = fread(magic, 1, 4, f) == 4 && memcmp(magic, "SDMO", 4) == 0 && fread(&ver, 4, 1, f) == 1 && ver == 1 &&
               fread(h, 4, 3, f) == 3 && fread(bbox, 4, 6, f) == 6 && h[2] > 0 && h[2] < (1 << 30);
     ok = ok && bbox[0] == -1.f && bbox[1] == -1.f && bbox[2] == -1.f && bbox[3] == 1.f && bbox[4] == 1.f && bbox[5] == 1.f;
+    // child [n] int32, depth [n] u8 padded to 4 bytes, far [n] float32: all there in full
+    ok = ok && bytes_left(f) >= 8 * (long long)h[2] + ((long long)h[2] + 3) / 4 * 4;
     std::vector<int32_t> child;
     std::vector<uint8_t> depth;
     std::vector<float> far;
     if (ok) {
         const size_t n = (size_t)h[2];
-        child.resize(n);
-        depth.resize((n + 3) / 4 * 4);
-        far.resize(n);
+        try {
+            child.resize(n);
+            depth.resize((n + 3) / 4 * 4);
+            far.resize(n);
+        } catch (const std::bad_alloc &) {
+            fclose(f);
+            set_error("%s: cannot hold %zu octree nodes in host memory", path, n);
+            return SAND_ENOMEM;
+        }
         ok = fread(child.data(), 4, n, f) == n && fread(depth.data(), 1, depth.size(), f) == depth.size() &&
              fread(far.data(), 4, n, f) == n;
     }

@@ -74,3 +74,44 @@ def test_sizes_without_a_device(B):
     # tracer state: grows with the rays, about 60 B per ray
     s1, s2 = L.sand_trace_state_bytes(1 << 16), L.sand_trace_state_bytes(1 << 17)
     assert 40 * (1 << 16) <= s2 - s1 <= 200 * (1 << 16)
+
+
+def test_model_file_fuzz(B, tmp_path):
+    """Truncations and single-byte corruptions of a model file give a status, never a crash
+    or an allocation sized by a corrupted count: EFORMAT for a broken header, size or
+    descriptor; a well-formed file parses (EUNSUPPORTED without a usable device, else OK)."""
+    import numpy as np
+    import synth
+    L = B.lib()
+    m = synth.siren_tmlp(2, 16, seed=3)
+    path = tmp_path / "m.tmlp"
+    synth.save_tmlp(str(path), m)
+    raw = path.read_bytes()
+    try:
+        import torch
+        good = B.SAND_OK if torch.cuda.is_available() else B.SAND_EUNSUPPORTED
+    except Exception:
+        good = B.SAND_EUNSUPPORTED
+    allowed = {B.SAND_EFORMAT, B.SAND_EINVAL, good}
+    h = ctypes.c_void_p()
+    g = np.random.Generator(np.random.PCG64(1))
+    cases = [raw[:k] for k in (0, 3, 4, 8, 20, 40, 47, 48, 52, len(raw) - 1)]
+    for _ in range(200):
+        b = bytearray(raw)
+        i = int(g.integers(0, 48))  # the header: magic, version, 7 ints, omega0, parameter count
+        b[i] = int(g.integers(0, 256))
+        cases.append(bytes(b))
+    # the parameter count set to the largest value the header accepts (2^31 - 1)
+    b = bytearray(raw)
+    b[40:48] = (2 ** 31 - 1).to_bytes(8, "little")
+    cases.append(bytes(b))
+    for k, data in enumerate(cases):
+        f = tmp_path / ("c%d.tmlp" % k)
+        f.write_bytes(data)
+        rc = L.sand_load_tmlp(str(f).encode(), 0, ctypes.byref(h))
+        assert rc in allowed, (k, rc, L.sand_last_error())
+        if rc == B.SAND_OK:
+            L.sand_free(h)
+    big = tmp_path / "big.tmlp"
+    big.write_bytes(cases[-1])
+    assert L.sand_load_tmlp(str(big).encode(), 0, ctypes.byref(h)) == B.SAND_EFORMAT
