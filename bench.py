@@ -174,8 +174,15 @@ def cpu_baseline(model, tree, pts, budget_s: float = 12.0):
     t0 = time.perf_counter()
     oracle.query(model, tree, pts[idx])
     dt = time.perf_counter() - t0
+    # the oracle's own full-depth mode on 20,000 lattice points (PCG64 seed 12), for its SAND / full ratio
+    kf = min(n, 20000)
+    idf = synth.sample_indices(n, kf, seed=12)
+    t0 = time.perf_counter()
+    oracle.full_depth(model, pts[idf])
+    dtf = time.perf_counter() - t0
     return {"value": k / dt, "unit": "queries/s", "cores": oracle.threads(), "kind": "oracle",
             "nproc": os.cpu_count(), "cpu": host_cpu(),
+            "full_depth_value": kf / dtf, "full_depth_sample": "%d lattice points (PCG64 seed 12), %.1f s" % (kf, dtf),
             "sample": "%d lattice points drawn with PCG64 seed 11 from the %d^3 lattice, SAND query (lookup + "
                       "T-MLP to each exit layer) in float64, %.1f s" % (k, GRID, dt)}
 
