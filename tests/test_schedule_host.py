@@ -44,7 +44,7 @@ def cuda_core_rows(n_tc, n, grid):
     return rows
 
 
-@pytest.mark.parametrize("n,grid", itertools.product([0, 1, 63, 64, 127, 128, 129, 511, 512, 513, 4097], [1, 3, 152]))
+@pytest.mark.parametrize("n,grid", list(itertools.product([0, 1, 63, 64, 127, 128, 129, 511, 512, 513, 4097], [1, 3, 152])))
 def test_every_row_once(n, grid):
     for n_tc in sorted({0, n, n // 2, min(n, 127), min(n, 129), max(0, n - 1)}):
         rows = tensor_core_rows(n_tc, grid) + cuda_core_rows(n_tc, n, grid)
