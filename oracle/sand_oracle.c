@@ -17,9 +17,8 @@
  *     + b_i) with act = sin(omega0 * .) (SIREN), max(0, .) (ReLU) or
  *     sin(omega0 (|.| + 1) .) (FINER, the variable-periodic sine of the
  *     SAND-FINER backbone; SAND cites FINER without restating its formula, so
- *     this activation is PARITY UNPINNED against the paper: its tests check
- *     only self-consistency — the gradient against central differences, the
- *     small-argument limit where it becomes SIREN, the sign symmetry),
+ *     this follows FINER's own definition, and its tests pin it to that
+ *     definition evaluated in 50-digit arithmetic on hand-set layers),
  *     t_i = a_i . h_i + c_i, and for multiplicative tails (Eq. 3) with i >= 2
  *     t_i = (a_i . h_i + c_i) (b_i . h_i + e_i); y_i = y_{i-1} + t_i, y_0 = 0.
  *     The result for exit layer d is y_d.

@@ -1,17 +1,20 @@
 """FINER backbone (variable-periodic sine sin(omega0 (|z| + 1) z)) through the C-ABI, against
-the FP64 oracle.  PARITY UNPINNED against the paper: SAND does not restate FINER's activation,
-so the oracle's FINER is pinned only by self-consistency (its own tests); these tests hold the
-CUDA paths to that oracle.
+the FP64 oracle.  SAND cites FINER without restating its activation; the oracle's FINER is
+pinned to FINER's published definition, evaluated in 50-digit arithmetic
+(tests/test_oracle_finer.py); these tests hold the CUDA paths to that oracle.
 
-Tolerances as for SIREN (1e-5 float32, 2e-3 16-bit, FP8 reported with the SIREN FP8 bounds),
-the gradient's scaled by the activation's larger slope omega0 (2 |z| + 1) <= 5 omega0 for the
-|z| <= 2 of these models.  Exit layers bit-exact.
+Tolerances: values as for SIREN (1e-5 float32, 2e-3 16-bit); float32 gradients 1e-5 omega0
+max|g| scaled by the activation's larger slope omega0 (2 |z| + 1) <= 5 omega0 for the |z| <= 2
+of these models; 16-bit gradients 3x the error of the float64 emulation of the same operand
+rounding on the same points (tests/quantised_emulation.py) plus that float32 bound; FP8 values
+at full depth 3x the emulated maximum error.  Exit layers bit-exact.
 """
 import numpy as np
 import pytest
 import torch
 
 import oracle
+import quantised_emulation as qe
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -48,8 +51,10 @@ def test_finer_sand_query(tail, prec):
     yg, g = m.query_grad(dev(pts), precision=prec)
     gscale = max(1.0, float(np.abs(g_ref).max()))
     gerr = float(np.abs(g.double().cpu().numpy() - g_ref).max())
-    gtol = (1e-5 * 5 * model.omega0 if prec.startswith("fp32") else {"fp16": 2.0 ** -10, "bf16": 2.0 ** -7}[prec]
-            * model.n_layers * 5) * gscale
+    gtol = 1e-5 * 5 * model.omega0 * gscale
+    if not prec.startswith("fp32"):
+        _, g_emu = qe.query(model, tree, pts, prec, grad=True)
+        gtol += 3.0 * float(np.abs(g_emu - g_ref).max())
     print("finer %s/%d grad err %.3g (max|g| %.3g, tol %.3g)" % (prec, tail, gerr, gscale, gtol))
     assert gerr <= gtol, (gerr, gtol)
     m.free()
@@ -60,9 +65,10 @@ def test_finer_fp8_and_full_depth():
     m = load(model)
     pts = synth.uniform_points(20001, seed=17)
     y_ref = oracle.full_depth(model, pts)
-    for prec, tol in (("fp32", 1e-5), ("fp8", 0.08)):
+    fp8_tol = 3.0 * qe.full_depth_error(model, "fp8")[0]
+    for prec, tol in (("fp32", 1e-5 * max(1.0, float(np.abs(y_ref).max()))), ("fp8", fp8_tol)):
         y = m.query(dev(pts), precision=prec, full_depth=True).double().cpu().numpy()
         err = float(np.abs(y - y_ref).max())
-        print("finer full depth %s err %.3g" % (prec, err))
-        assert err <= tol * max(1.0, float(np.abs(y_ref).max())), (prec, err)
+        print("finer full depth %s err %.3g (bound %.3g)" % (prec, err, tol))
+        assert err <= tol, (prec, err, tol)
     m.free()

@@ -13,6 +13,7 @@ import pytest
 import torch
 
 import oracle
+import quantised_emulation as qe
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -157,10 +158,13 @@ def test_relu_fourier_model(prec):
     y, el = m.query(dev(pts), precision=prec, exit_layers=True)
     np.testing.assert_array_equal(el.cpu().numpy().astype(np.int32), d_ref)
     scale = max(1.0, float(np.abs(y_ref).max()))
-    # ReLU activations are unbounded, unlike sines; for bf16 operands (unit roundoff 2^-9 per
-    # operand, two operands per product) the relative error grows about linearly with depth,
-    # so the bound is 2^-8 per layer of the output scale.
-    tol = (2.0 ** -8) * model.n_layers * scale if prec == "bf16" else TOL[prec] * scale
+    # ReLU activations are unbounded, unlike sines, so bf16 operands (8 significant bits) miss
+    # the 2e-3 bar on this model; its bound is twice the error of the float64 emulation of the
+    # same operand rounding on these points (tests/quantised_emulation.py; 3.2e-3 here)
+    if prec == "bf16":
+        tol = 2.0 * float(np.abs(qe.query(model, tree, pts, "bf16") - y_ref).max())
+    else:
+        tol = TOL[prec] * scale
     check(y, y_ref, tol, "relu-ff/" + prec)
     m.free()
 
