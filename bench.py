@@ -243,12 +243,8 @@ def job_throughput(points_per_rank: int, world: int, max_seconds: float) -> floa
 
 def serve_models(sand):
     """The three resident models of the serving workload, each with its own level-7 octree."""
-    specs = [(synth.siren_tmlp(8, 256, seed=1), synth.scene_octree(7, 8)),
-             (synth.siren_tmlp(8, 336, seed=2), synth.scene_octree(7, 8, transform=synth.rotation([0, 1, 0], 0.5), scale=0.95)),
-             (synth.relu_ff_tmlp(6, 128, n_freq=64, sigma=10.0, seed=3),
-              synth.scene_octree(7, 6, transform=synth.rotation([1, 1, 0], 0.7), scale=0.9))]
     models = []
-    for model, tree in specs:
+    for model, tree in synth.serve_specs():
         m = sand.Model.from_params(*model.header_ints(), model.omega0, model.flat(), device=0)
         m.set_depth_map(tree.max_level, tree.n_layers, tree.child, tree.depth, tree.far)
         models.append(m)
@@ -278,75 +274,167 @@ def serve_requests(count: int, seed: int):
     return pool
 
 
-def serve_bench(sand, models, precision, pool, run_s: float, mem_budget: int = 16 << 30):
-    """Saturation throughput (closed burst of the pool) and Poisson open-loop runs at 0.5x
-    and 0.8x of it: p50 / p99 request latency and aggregate queries/s."""
+def _open_loop(sand, srv, pool, lam: float, seconds: float, g):
+    """Poisson arrivals at lam requests/s for `seconds`, each a uniformly drawn pool entry with
+    an output buffer of its own (buffers are recycled once their request completed, and a new
+    pinned buffer is made when none is free), so no arrival is ever dropped.  Returns the
+    server's report plus the arrivals submitted and the most requests outstanding at once."""
+    import collections
     import threading
     import torch
+    free_out = [[] for _ in pool]
+    pending = collections.deque()
+    lock = threading.Lock()
+    done = threading.Event()
+    outstanding = [0, 0]
+
+    def waiter():
+        while True:
+            with lock:
+                item = pending.popleft() if pending else None
+            if item is None:
+                if done.is_set():
+                    return
+                time.sleep(0.0002)
+                continue
+            t, i, buf = item
+            srv.wait(t)
+            with lock:
+                free_out[i].append(buf)
+                outstanding[0] -= 1
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    t_end = time.perf_counter() + seconds
+    nxt = time.perf_counter()
+    sent = 0
+    while True:
+        nxt += g.exponential(1.0 / lam)
+        if nxt >= t_end:
+            break
+        while time.perf_counter() < nxt:
+            time.sleep(max(0.0, min(0.002, nxt - time.perf_counter())))
+        i = int(g.integers(len(pool)))
+        with lock:
+            buf = free_out[i].pop() if free_out[i] else None
+        if buf is None:
+            buf = torch.empty(pool[i][1].shape[0], dtype=torch.float32).pin_memory()
+        t = srv.submit(pool[i][0], pool[i][1], buf)
+        with lock:
+            pending.append((t, i, buf))
+            outstanding[0] += 1
+            outstanding[1] = max(outstanding[1], outstanding[0])
+        sent += 1
+    done.set()
+    th.join()
+    st = srv.stats()
+    st.update({"offered_requests_per_s": lam, "submitted": sent, "dropped": 0, "max_outstanding": outstanding[1],
+               "seconds": seconds})
+    return st
+
+
+def serve_bench(sand, models, precision, pool, run_s: float, sweep_s: float, mem_budget: int = 16 << 30):
+    """Continuous batching over the three resident models: a closed burst of the pool estimates
+    the saturation rate; open-loop Poisson runs of sweep_s seconds at 0.25 .. 1.5 of that
+    estimate find the saturation throughput (the largest completed queries/s); then open-loop
+    runs of run_s seconds at 0.5x and 0.8x of saturation report p50 / p99 request latency
+    (submit to result) and aggregate queries/s."""
+    import torch
     precs = {"bf16": ["bf16", "bf16", "bf16"], "fp32": ["fp32", "fp32_simt", "fp32"]}[precision]
-    out = {"precision_per_model": precs}
-    srv = sand.Server(models, precision=precs, n_streams=4, mem_budget=mem_budget, max_batch_points=1 << 22)
+    out = {"precision_per_model": precs, "n_streams": 4, "mem_budget": mem_budget}
+
+    def server():
+        return sand.Server(models, precision=precs, n_streams=4, mem_budget=mem_budget, max_batch_points=1 << 22)
+
     outs = [torch.empty(p.shape[0], dtype=torch.float32).pin_memory() for _, p in pool]
+    srv = server()
     for i in range(min(4, len(pool))):  # warm up
         srv.wait(srv.submit(pool[i][0], pool[i][1], outs[i]))
     srv.close()
-    srv = sand.Server(models, precision=precs, n_streams=4, mem_budget=mem_budget, max_batch_points=1 << 22)
+    srv = server()
     t0 = time.perf_counter()
     tk = [srv.submit(m, p, outs[i]) for i, (m, p) in enumerate(pool)]
     for t in tk:
         srv.wait(t)
-    sat_s = time.perf_counter() - t0
-    pts_total = sum(p.shape[0] for _, p in pool)
+    burst_s = time.perf_counter() - t0
     srv.close()
-    sat_qps = pts_total / sat_s
-    out["saturation_qps"] = sat_qps
+    pts_total = sum(p.shape[0] for _, p in pool)
     mean_pts = pts_total / len(pool)
+    burst_qps = pts_total / burst_s
+    out["burst_qps"] = burst_qps
     g = np.random.Generator(np.random.PCG64(99))
-    for frac in (0.5, 0.8):
-        lam = frac * sat_qps / mean_pts  # requests per second
-        srv = sand.Server(models, precision=precs, n_streams=4, mem_budget=mem_budget, max_batch_points=1 << 22)
-        free = list(range(len(pool)))
-        lock = threading.Lock()
-        pending = []
-        done = threading.Event()
-
-        def waiter():
-            while not (done.is_set() and not pending):
-                with lock:
-                    item = pending.pop(0) if pending else None
-                if item is None:
-                    time.sleep(0.0005)
-                    continue
-                t, i = item
-                srv.wait(t)
-                with lock:
-                    free.append(i)
-
-        th = threading.Thread(target=waiter)
-        th.start()
-        t_end = time.perf_counter() + run_s
-        nxt = time.perf_counter()
-        sent = 0
-        while time.perf_counter() < t_end:
-            nxt += g.exponential(1.0 / lam)
-            while time.perf_counter() < nxt:
-                time.sleep(max(0.0, min(0.002, nxt - time.perf_counter())))
-            with lock:
-                i = free.pop(int(g.integers(len(free)))) if free else None
-            if i is None:
-                continue  # every buffer is in flight: the request is dropped (counted below)
-            t = srv.submit(pool[i][0], pool[i][1], outs[i])
-            with lock:
-                pending.append((t, i))
-            sent += 1
-        done.set()
-        th.join()
-        st = srv.stats()
+    sweep = []
+    for frac in (0.25, 0.5, 0.75, 1.0, 1.25, 1.5):
+        srv = server()
+        st = _open_loop(sand, srv, pool, frac * burst_qps / mean_pts, sweep_s, g)
         srv.close()
-        out["load_%.1f" % frac] = {"offered_requests_per_s": lam, "requests": st["requests"], "p50_ms": st["p50_ms"],
-                                   "p99_ms": st["p99_ms"], "max_ms": st["max_ms"], "queries_per_s": st["queries_per_s"],
-                                   "batches": st["batches"], "seconds": run_s}
+        sweep.append({"offered_fraction_of_burst": frac, "offered_queries_per_s": frac * burst_qps,
+                      "queries_per_s": st["queries_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                      "requests": st["requests"], "max_outstanding": st["max_outstanding"]})
+    sat_qps = max(e["queries_per_s"] for e in sweep)
+    out["lambda_sweep"] = sweep
+    out["saturation_qps"] = sat_qps
+    for frac in (0.5, 0.8):
+        srv = server()
+        st = _open_loop(sand, srv, pool, frac * sat_qps / mean_pts, run_s, g)
+        srv.close()
+        out["load_%.1f" % frac] = {k: st[k] for k in ("offered_requests_per_s", "submitted", "dropped", "requests",
+                                                      "batches", "p50_ms", "p99_ms", "max_ms", "queries_per_s",
+                                                      "max_outstanding", "seconds")}
     return out
+
+
+def paper_variants(sand, local: int, steps: int, prec: str, peak_tflops: float, hbm_gbs: float):
+    """The benchmark lattice query as the paper states the method: (a) multiplicative tails for
+    layers >= 2 (Eq. 3), and (b) the far-field depth map, whose leaves away from the surface
+    hold exit layer 0 and answer with the SDF stored at their centre (Eq. 7).  Each: SAND
+    queries/s, the T-MLP kernel's algorithmic TFLOP/s against the precision's peak, the error
+    against the oracle on 20,000 sampled lattice points; (b) also the whole step's algorithmic
+    traffic (12 B read + 4 B written per point) against the HBM copy rate."""
+    import torch
+    import oracle
+    pts = synth.lattice(GRID)
+    n = len(pts)
+    x = torch.from_numpy(pts).cuda()
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    idx = synth.sample_indices(n, 20000, seed=11)
+    res = {"lattice": "%d^3 (%d points)" % (GRID, n), "precision": prec}
+    for name, tail, far in (("mult_tails", synth.TAIL_MULT, False), ("far_field", synth.TAIL_LINEAR, True)):
+        model = synth.siren_tmlp(N_LAYERS, WIDTH, seed=SEED, tail_kind=tail)
+        tree = synth.scene_octree(7, N_LAYERS, far_field=far)
+        m = sand.Model.from_params(*model.header_ints(), model.omega0, model.flat(), device=local)
+        m.set_depth_map(tree.max_level, tree.n_layers, tree.child, tree.depth, tree.far)
+        ws = m.workspace(n)
+        for _ in range(3):
+            m.query(x, precision=prec, out=out, workspace=ws)
+        torch.cuda.synchronize()
+        counts = np.array(m.stats(ws)["count"][:N_LAYERS + 1], np.int64)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k in range(steps):
+            m.query(x, precision=prec, out=out, workspace=ws, events=ev[k])
+        t1.record(stream)
+        torch.cuda.synchronize()
+        step_ms = t0.elapsed_time(t1) / steps
+        mlp_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / steps
+        flops = float((flops_per_point(np.arange(N_LAYERS + 1), WIDTH, tail == synth.TAIL_MULT) * counts).sum())
+        achieved = flops / (mlp_ms / 1e3) / 1e12
+        y_ref = oracle.query(model, tree, pts[idx])
+        entry = {"queries_per_s": n / (step_ms / 1e3), "ms_per_step": step_ms, "tmlp_ms": mlp_ms,
+                 "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                              "frac": achieved / peak_tflops, "kernel": KERNEL_NAME[prec]},
+                 "max_abs_err_vs_oracle_20k": float(np.abs(out.cpu().numpy()[idx].astype(np.float64) - y_ref).max()),
+                 "exit_layer_histogram": {str(d): int(c) for d, c in enumerate(counts)}}
+        if far:
+            gbs = 16.0 * n / (step_ms / 1e3) / 1e9
+            entry["far_points"] = int(counts[0])
+            entry["hbm"] = {"bytes_per_point": 16, "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s",
+                            "frac": gbs / hbm_gbs}
+        res[name] = entry
+        m.free()
+    return res
 
 
 def precision_variant(sand, local: int, steps: int, grid: int = 512, n_err: int = 1 << 20):
@@ -661,7 +749,10 @@ def main():
                     help="small profiling case: only (warmup + steps) SAND queries on a grid^3 lattice, or full-depth "
                          "queries on grid^3 uniform points; prints one line")
     ap.add_argument("--grid", type=int, default=GRID)
-    ap.add_argument("--serve-seconds", type=float, default=6.0, help="length of each open-loop serving run (0 = skip)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="length of the bf16 open-loop serving runs at 0.5x and 0.8x of saturation (0 = skip "
+                         "serving; the float32 runs take a third of it)")
+    ap.add_argument("--sweep-seconds", type=float, default=4.0, help="length of each run of the serving load sweep")
     ap.add_argument("--peaks", action="store_true", help="measure GEMM, FMA and sine peaks of this GPU; prints one line")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -805,7 +896,8 @@ def main():
     if rank == 0 and args.serve_seconds > 0:
         smodels = serve_models(sand)
         pool = serve_requests(40, seed=5)
-        serve = {p: serve_bench(sand, smodels, p, pool, args.serve_seconds) for p in ("bf16", "fp32")}
+        serve = {"bf16": serve_bench(sand, smodels, "bf16", pool, args.serve_seconds, args.sweep_seconds),
+                 "fp32": serve_bench(sand, smodels, "fp32", pool, args.serve_seconds / 3, args.sweep_seconds)}
         for sm in smodels:
             sm.free()
 
@@ -828,6 +920,10 @@ def main():
     variant = None
     if rank == 0 and not args.no_variants:
         variant = precision_variant(sand, local, max(3, K // 4))
+
+    paperv = None
+    if rank == 0 and not args.no_variants and prec != "fp32_simt":
+        paperv = paper_variants(sand, local, max(3, K // 4), prec, roof["peak"], pk.get("hbm_gbs", 6800.0))
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -866,6 +962,7 @@ def main():
         "cpu_baseline": cpu,
         "serve": serve,
         "precision_variant": variant,
+        "paper_variants": paperv,
         "sphere_trace": tr,
         "depth_map_build": mapb,
         "dynamic_exit": dynb,

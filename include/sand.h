@@ -184,8 +184,11 @@ sand_status sand_query_sdf_host(sand_model m, const float *h_points, int64_t n, 
  * SAND_NOALLOC_MAX_POINTS points (about 17 MiB), which each GPU using it keeps
  * until the process exits.  n above SAND_NOALLOC_MAX_POINTS returns
  * SAND_EINVAL.  Nothing is allocated: the precision's device weights must
- * already exist (SAND_FP32_SIMT always; a tensor-core precision after one
- * sand_query_sdf with it), else SAND_EUNSUPPORTED.  The first call on a device
+ * already exist, else SAND_EUNSUPPORTED.  SAND_FP32_SIMT's always do; a model
+ * keeps the packed weights of one tensor-core precision at a time, those of
+ * its most recent tensor-core query (or of sand_server_create), so query once
+ * with the precision through sand_query_sdf first.  A precision the model
+ * cannot take at all is SAND_EUNSUPPORTED with a message that says so.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress), so make it
  * before any stream capture.  Calls share the array: calls that may overlap on
  * the GPU (unordered streams) race and corrupt each other's results. */
@@ -217,7 +220,9 @@ sand_status sand_query_sdf_dynamic(sand_model m, const float *d_points, int64_t 
  * Outputs (device, caller-owned, each nullable): d_t [n] final t, d_state [n],
  * d_steps [n] queries made for the ray, d_grad [n][3] the input gradient of
  * y at the hit points (the surface normal direction, not normalised; 0 for rays
- * that did not hit), evaluated on the CUDA cores in float32.
+ * that did not hit), from a gradient query in qopts' precision (on the tensor
+ * cores for SAND_FP32, SAND_FP16, SAND_BF16 and SAND_FP8; on the CUDA cores for
+ * SAND_FP32_SIMT).
  * qopts: precision and max_depth apply to every step; its other fields must be
  * zero (the tracer owns its workspace: a grow-only device buffer of
  * sand_trace_state_bytes(n_rays) kept by the model, so trace calls on one model
@@ -289,7 +294,9 @@ typedef struct {
     int32_t precision;          /* sand_precision of every query */
     size_t mem_budget;          /* device arena for in-flight batches (default 1 GiB) */
     int64_t max_batch_points;   /* upper bound of points per batch (default 2^22; a larger request runs alone) */
-    const int32_t *model_precision; /* optional [n_models]: per-model sand_precision overriding `precision` */
+    const int32_t *model_precision; /* optional [n_models]: per-model sand_precision overriding `precision`;
+                                   one handle listed twice may not take two tensor-core precisions
+                                   (a model packs one at a time): SAND_EINVAL */
 } sand_server_opts;
 typedef struct {
     int64_t requests, batches, points;   /* completed so far */

@@ -209,6 +209,9 @@ static sand_status model_precheck(sand_model m) {
 int model_device(sand_model m) { return m->device; }
 int model_layers(sand_model m) { return m->desc.n_layers; }
 bool model_has_map(sand_model m) { return m->map_level >= 0; }
+bool model_precision_supported(sand_model m, int precision) {
+    return precision == SAND_FP32_SIMT || tc_supported(m->desc, precision);
+}
 bool model_precision_ready(sand_model m, int precision) {
     if (precision == SAND_FP32_SIMT) return true;
     return m->tc.packed_precision == precision && m->tc.d_pack != nullptr;
@@ -394,10 +397,9 @@ static sand_status run_query(sand_model m, const float *d_points, int64_t n, flo
     if (!o.full_depth && m->map_level < 0) { set_error("no depth map loaded"); return SAND_ENOMAP; }
     if (o.full_depth && o.d_exit_layers) { set_error("exit layers are not produced in full-depth mode"); return SAND_EINVAL; }
     if (o.full_depth && d_count) { set_error("full-depth mode needs a host point count"); return SAND_EINVAL; }
-    // gradients run on the tensor cores too; the CUDA-core kernel serves SAND_FP32_SIMT, and
-    // float32 gradients of widths the tensor-core path does not take
-    const bool simt = o.precision == SAND_FP32_SIMT ||
-                      (d_grad != nullptr && o.precision == SAND_FP32 && !tc_supported(m->desc, o.precision));
+    // the CUDA-core kernel serves SAND_FP32_SIMT only; every other precision runs on the tensor
+    // cores or is refused (no silent switch of kernels)
+    const bool simt = o.precision == SAND_FP32_SIMT;
     if (o.all_tails && simt) { set_error("all_tails runs on the tensor-core precisions only"); return SAND_EUNSUPPORTED; }
     if (!simt && !tc_supported(m->desc, o.precision)) {
         set_error("precision %d is not supported for this model on the tensor-core path", o.precision);

@@ -133,6 +133,7 @@ cudaError_t launch_init_header(void *ws, cudaStream_t s);
 // Model facts for entry points outside api.cu.
 int model_device(sand_model m);
 bool model_has_map(sand_model m);
+bool model_precision_supported(sand_model m, int precision);  // some kernel of the library takes it
 bool model_precision_ready(sand_model m, int precision);  // device weights for `precision` exist already
 sand_status model_prepare(sand_model m, int precision);   // pack device weights for `precision` (may allocate)
 // A SAND query of min(n, *d_count) points whose count is produced on the device (buffers

@@ -56,9 +56,14 @@ extern "C" sand_status sand_query_sdf_noalloc(sand_model m, const float *d_point
         set_error("sand_query_sdf_noalloc uses its own static scratch; pass d_workspace = NULL");
         return SAND_EINVAL;
     }
+    if (!model_precision_supported(m, o.precision)) {
+        set_error("precision %d is not supported for this model", o.precision);
+        return SAND_EUNSUPPORTED;
+    }
     if (!model_precision_ready(m, o.precision)) {
-        set_error("precision %d has no packed device weights yet; run one sand_query_sdf with it first "
-                  "(that call may allocate) or use SAND_FP32_SIMT", o.precision);
+        set_error("precision %d has no packed device weights now (a model keeps those of its most recent "
+                  "tensor-core precision only); run one sand_query_sdf with it first (that call may allocate) "
+                  "or use SAND_FP32_SIMT", o.precision);
         return SAND_EUNSUPPORTED;
     }
     const int dev = model_device(m);

@@ -311,6 +311,17 @@ sand_status sand_server_create(const sand_model *models, int n_models, const san
     if (S->opts.model_precision)
         for (int i = 0; i < n_models; ++i) S->precision[i] = S->opts.model_precision[i];
     S->opts.model_precision = nullptr;  // copied; the caller's array need not outlive this call
+    // a model keeps the packed weights of one tensor-core precision: one handle served in two
+    // would repack (free and allocate) inside the serving loop
+    for (int i = 0; i < n_models; ++i)
+        for (int j = i + 1; j < n_models; ++j)
+            if (models[i] == models[j] && S->precision[i] != S->precision[j] && S->precision[i] != SAND_FP32_SIMT &&
+                S->precision[j] != SAND_FP32_SIMT) {
+                delete S;
+                set_error("models %d and %d are one handle with two tensor-core precisions (%d, %d)", i, j,
+                          S->precision[i], S->precision[j]);
+                return SAND_EINVAL;
+            }
     for (int i = 0; i < n_models; ++i) {  // pack tensor-core weights now: the serving loop allocates nothing
         sand_status st = model_prepare(models[i], S->precision[i]);
         if (st) {

@@ -485,6 +485,16 @@ def pinhole_rays(width: int, height: int, fov_y_deg: float = 45.0, radius: float
 # --------------------------------------------------------------------------
 # Named workloads
 # --------------------------------------------------------------------------
+def serve_specs():
+    """The three resident models of the serving workload, each with its own level-7 octree of
+    the analytic scene (rotated and scaled per model): 8 x 256 SIREN (seed 1), 8 x 336 SIREN
+    (seed 2), 6 x 128 ReLU on 64 Fourier features (sigma 10, seed 3)."""
+    return [(siren_tmlp(8, 256, seed=1), scene_octree(7, 8)),
+            (siren_tmlp(8, 336, seed=2), scene_octree(7, 8, transform=rotation([0, 1, 0], 0.5), scale=0.95)),
+            (relu_ff_tmlp(6, 128, n_freq=64, sigma=10.0, seed=3),
+             scene_octree(7, 6, transform=rotation([1, 1, 0], 0.7), scale=0.9))]
+
+
 def config_tiny():
     """4 x 64 SIREN (seed 0), 8^3 voxel sphere map, 32^3 lattice."""
     return siren_tmlp(4, 64, seed=0), voxel_sphere_octree(3, 0.5), lattice(32)

@@ -1,9 +1,17 @@
 """Serving loop: continuous batching over resident models (include/sand.h, sand_server_*).
 
-Results must be the same alone and in the mix (float32 tolerance 1e-5; the
-kernels compute every row independently, so they are in fact expected to be
-bit-identical), requests are admitted by device memory, and the latency report
-is consistent.
+The serving workload's three resident models (8 x 256 SIREN, 8 x 336 SIREN, 6 x 128 ReLU on
+Fourier features, each with its own level-7 octree: synth.serve_specs) take a mix of
+marching-cubes blocks and point batches from four client threads.  Every result must be
+* the same in the mix as the same request run alone through sand_query_sdf (the kernels
+  compute every row independently, so it is in fact expected to be bit-identical; the
+  identical count is printed and required), and
+* within the precision's tolerance of the FP64 oracle: 1e-5 in float32; in bf16 2e-3 for the
+  sine models and, for the ReLU model (unbounded activations), twice the error of the float64
+  emulation of the same bf16 operand rounding on the request's points.
+Precision mixes: all bf16 (the precision the serving p99 is quoted at), the float32 mix the
+benchmark serves (the 8 x 336 model on the CUDA cores) and all on the CUDA cores.
+Requests are admitted by device memory, and the latency report is consistent.
 """
 import threading
 
@@ -11,18 +19,20 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
+import quantised_emulation as qe
 import synth
 
 pytestmark = pytest.mark.gpu
 
+MIXES = {"bf16": ["bf16"] * 3, "fp32": ["fp32", "fp32_simt", "fp32"], "fp32_simt": ["fp32_simt"] * 3}
+TOL = {"fp32": 1e-5, "fp32_simt": 1e-5, "bf16": 2e-3}
+
 
 def _models():
     from paper_2604_25936_gb300 import Model
-    specs = [(synth.siren_tmlp(8, 256, seed=1), synth.scene_octree(7, 8)),
-             (synth.relu_ff_tmlp(6, 128, n_freq=64, sigma=10.0, seed=3), synth.scene_octree(7, 6, transform=synth.rotation([1, 1, 0], 0.7), scale=0.9)),
-             (synth.siren_tmlp(4, 64, seed=0), synth.voxel_sphere_octree())]
     out = []
-    for model, tree in specs:
+    for model, tree in synth.serve_specs():
         m = Model.from_params(*model.header_ints(), model.omega0, model.flat(), device=0)
         m.set_depth_map(tree.max_level, tree.n_layers, tree.child, tree.depth, tree.far)
         out.append(m)
@@ -35,23 +45,25 @@ def _requests(seed, count):
     for i in range(count):
         kind = g.integers(3)
         if kind == 0:
-            side = int(g.choice([8, 16, 32, 48]))
+            side = int(g.choice([8, 16, 32, 40]))
             pts = synth.lattice(side)
         elif kind == 1:
-            pts = g.uniform(-1, 1, (int(g.integers(1, 70000)), 3)).astype(np.float32)
+            pts = g.uniform(-1, 1, (int(g.integers(1, 40000)), 3)).astype(np.float32)
         else:
             pts = g.uniform(-1.2, 1.2, (int(g.choice([1, 2, 127, 129, 4097])), 3)).astype(np.float32)
         reqs.append((int(g.integers(3)), torch.from_numpy(pts).pin_memory()))
     return reqs
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp32_simt"])
-def test_results_alone_and_in_the_mix(precision):
+@pytest.mark.parametrize("mix", sorted(MIXES))
+def test_results_alone_in_the_mix_and_against_the_oracle(mix):
     from paper_2604_25936_gb300 import Server
+    specs = synth.serve_specs()
     models = _models()
-    reqs = _requests(7, 60)
-    alone = [models[m].query(p.cuda(), precision=precision).cpu() for m, p in reqs]
-    srv = Server(models, precision=precision, n_streams=3, mem_budget=256 << 20, max_batch_points=1 << 17)
+    precs = MIXES[mix]
+    reqs = _requests(7, 48)
+    alone = [models[m].query(p.cuda(), precision=precs[m]).cpu() for m, p in reqs]
+    srv = Server(models, precision=precs, n_streams=3, mem_budget=256 << 20, max_batch_points=1 << 17)
     tickets = [None] * len(reqs)
 
     def client(idx):
@@ -63,27 +75,45 @@ def test_results_alone_and_in_the_mix(precision):
         t.start()
     for t in threads:
         t.join()
-    identical = 0
+    identical = [0, 0, 0]
+    count = [0, 0, 0]
+    worst = [0.0, 0.0, 0.0]
     for i, (m, p) in enumerate(reqs):
         out, lat = srv.wait(tickets[i])
         assert lat >= 0
         err = (out.double() - alone[i].double()).abs().max().item() if out.numel() else 0.0
-        assert err <= 1e-5, "request %d (model %d, n %d): max |mix - alone| = %g" % (i, m, p.shape[0], err)
-        identical += int(torch.equal(out, alone[i]))
+        assert err <= TOL[precs[m]], "request %d (model %d, n %d): max |mix - alone| = %g" % (i, m, p.shape[0], err)
+        identical[m] += int(torch.equal(out, alone[i]))
+        count[m] += 1
+        if not out.numel():
+            continue
+        model, tree = specs[m]
+        pts = p.numpy()
+        y_ref = oracle.query(model, tree, pts)
+        e = float(np.abs(out.double().numpy() - y_ref).max())
+        if precs[m] == "bf16" and model.activation == synth.ACT_RELU:
+            tol = 2.0 * float(np.abs(qe.query(model, tree, pts, "bf16") - y_ref).max())
+        else:
+            tol = TOL[precs[m]] * max(1.0, float(np.abs(y_ref).max()))
+        assert e <= tol, "request %d (model %d, %s, n %d): max |mix - oracle| = %g > %g" % (
+            i, m, precs[m], p.shape[0], e, tol)
+        worst[m] = max(worst[m], e)
+    for k in range(3):
+        print("serve %s model %d (%s): %d/%d requests identical alone and in the mix, max |err| vs oracle %.3g"
+              % (mix, k, precs[k], identical[k], count[k], worst[k]))
     st = srv.stats()
     assert st["requests"] == len(reqs) and st["points"] == sum(p.shape[0] for _, p in reqs)
     assert st["batches"] < len(reqs)  # requests were batched together
     assert 0 < st["p50_ms"] <= st["p99_ms"] <= st["max_ms"]
     srv.close()
-    assert identical == len(reqs)
+    assert sum(identical) == len(reqs)
 
 
 def test_admission_by_memory_and_errors():
     from paper_2604_25936_gb300 import SandError, Server
     models = _models()
-    from paper_2604_25936_gb300 import binding
     budget = 8 << 20  # fits about 200K points per batch
-    srv = Server(models, precision="fp32", n_streams=3, mem_budget=budget, max_batch_points=1 << 20)
+    srv = Server(models, precision=MIXES["fp32"], n_streams=3, mem_budget=budget, max_batch_points=1 << 20)
     g = np.random.Generator(np.random.PCG64(11))
     reqs = [g.uniform(-1, 1, (100000, 3)).astype(np.float32) for _ in range(12)]
     tickets = [srv.submit(0, p) for p in reqs]
@@ -98,4 +128,15 @@ def test_admission_by_memory_and_errors():
     assert srv.wait(empty)[0].size == 0
     with pytest.raises(SandError, match="EINVAL"):
         srv.submit(5, reqs[0])
+    srv.close()
+
+
+def test_one_handle_two_tensor_core_precisions_is_refused():
+    """A model packs one tensor-core precision at a time; serving one handle in two would repack
+    inside the serving loop, so the server refuses it (the CUDA-core precision needs no packing)."""
+    from paper_2604_25936_gb300 import SandError, Server
+    models = _models()
+    with pytest.raises(SandError, match="EINVAL"):
+        Server([models[0], models[0]], precision=["fp32", "bf16"])
+    srv = Server([models[0], models[0]], precision=["bf16", "fp32_simt"])
     srv.close()
