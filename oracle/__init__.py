@@ -52,6 +52,7 @@ def _load():
             lib.oracle_query.argtypes = [P, ctypes.c_double, P, ctypes.c_int, P, P, P, P, ctypes.c_int64,
                                          ctypes.c_int, P, P, P]
             lib.oracle_preact_margin.argtypes = [P, ctypes.c_double, P, P, ctypes.c_int64, P, ctypes.c_int, P]
+            lib.oracle_train_grad.argtypes = [P, ctypes.c_double, P, P, P, ctypes.c_int64, P, P]
             lib.oracle_param_count.argtypes = [P]
             lib.oracle_param_count.restype = ctypes.c_longlong
             lib.oracle_threads.restype = ctypes.c_int
@@ -252,3 +253,38 @@ def dynamic_exit(model, points, r: float):
     stop[:, -1] = True
     d = np.argmax(stop, axis=1) + 1
     return ys[np.arange(len(d)), d - 1], d.astype(np.int64), ys
+
+
+# ---------------------------------------------------------------------------------------------
+# Training (Sec. 3.3): the loss over every tail (Eq. 4 with the L1 SDF loss of Eq. 8) and Adam
+# ---------------------------------------------------------------------------------------------
+def train_grad(model, points, gt):
+    """The training loss L = sum_i (1/n) sum_x |y_i(x) - gt(x)| (Eq. 4 / Eq. 8) and its gradient
+    with respect to every parameter, as a float64 vector in the parameter-block order of
+    model.flat() (a Fourier matrix is not trained: its entries are 0).  |r|' = sign(r), sign(0)
+    = 0.  Returns (loss, grad)."""
+    hdr, w0, params = _model_args(model)
+    p = _pts(points)
+    n = p.shape[0]
+    t = np.ascontiguousarray(np.asarray(gt, np.float32).reshape(-1))
+    if t.size != n or n == 0:
+        raise ValueError("need one target per point and at least one point")
+    loss = np.zeros(1, np.float64)
+    grad = np.empty(params.size, np.float64)
+    rc = _load().oracle_train_grad(_ptr(hdr), w0, _ptr(params), _ptr(p), _ptr(t), n, _ptr(loss), _ptr(grad))
+    if rc:
+        raise RuntimeError("oracle_train_grad failed: %d" % rc)
+    return float(loss[0]), grad
+
+
+def adam_step(params, grad, m, v, step: int, lr: float = 1e-4, beta1: float = 0.9, beta2: float = 0.999,
+              eps: float = 1e-8):
+    """One Adam update (Kingma & Ba 2015, Algorithm 1) in float64, the optimiser of Sec. 4.1:
+    m <- b1 m + (1 - b1) g;  v <- b2 v + (1 - b2) g^2;  p <- p - lr (m / (1 - b1^t)) /
+    (sqrt(v / (1 - b2^t)) + eps), t = step >= 1.  Returns the new (params, m, v)."""
+    g = np.asarray(grad, np.float64)
+    m = beta1 * np.asarray(m, np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, np.float64) + (1.0 - beta2) * g * g
+    mh = m / (1.0 - beta1 ** step)
+    vh = v / (1.0 - beta2 ** step)
+    return np.asarray(params, np.float64) - lr * mh / (np.sqrt(vh) + eps), m, v

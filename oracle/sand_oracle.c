@@ -318,3 +318,154 @@ int oracle_query(const int32_t *hdr, double omega0, const float *params,
     }
     return bad ? -2 : 0;
 }
+
+/* ------------------------------------------------------------------ training loss and gradient
+ * The T-MLP training objective (Sec. 3.3, Eq. 4 with the L1 SDF loss of Eq. 8):
+ *     L = sum_{i=1..L} (1/n) sum_x | y_i(x) - y_gt(x) |,
+ * y_i the cumulative output up to tail i (Eq. 2 / Eq. 3).  Its gradient with respect to every
+ * trained parameter (W_l, b_l, tail weights and biases; a Fourier matrix B is fixed, gradient
+ * 0) by reverse-mode chain rule, per point in double, summed over the points.  The derivative
+ * of |r| is taken as sign(r) with sign(0) = 0.
+ * With G_k = (1/n) sum_{i>=k} sign(y_i - y_gt) = dL/dt_k (y_i = t_1 + ... + t_i), walking
+ * l = L .. 1 with g = dL/dh_l (0 above layer L):
+ *   linear tail:  dL/da_l += G_l h_l,  dL/dc_l += G_l,  g += G_l a_l;
+ *   mult. tail:   t_l = ta tb with ta = a.h + c, tb = b.h + e:  dL/da += G tb h, dL/dc += G tb,
+ *                 dL/db += G ta h, dL/de += G ta, g += G (tb a + ta b);
+ *   delta = g * act'(u_l);  dL/db_l += delta;  dL/dW_l += delta h_{l-1}^T;  g <- W_l^T delta.
+ * loss: [1]; grad: [n_params] in the parameter-block layout.  Each thread sums its points into
+ * its own block; the blocks are added in thread order. */
+static double act_slope(const model_t *M, double u) {
+    if (M->act == ORACLE_ACT_RELU) return u > 0.0 ? 1.0 : 0.0;
+    if (M->act == ORACLE_ACT_FINER) return M->omega0 * (2.0 * fabs(u) + 1.0) * cos(M->omega0 * (fabs(u) + 1.0) * u);
+    return M->omega0 * cos(M->omega0 * u);
+}
+
+static double act_value(const model_t *M, double u) {
+    if (M->act == ORACLE_ACT_RELU) return u > 0.0 ? u : 0.0;
+    if (M->act == ORACLE_ACT_FINER) return sin(M->omega0 * (fabs(u) + 1.0) * u);
+    return sin(M->omega0 * u);
+}
+
+int oracle_train_grad(const int32_t *hdr, double omega0, const float *params, const float *pts,
+                      const float *gt, int64_t n, double *loss, double *grad) {
+    model_t M;
+    if (model_init(&M, hdr, omega0, params)) return -1;
+    if (n <= 0) return -3;
+    const int L = M.L, W = M.W, D = M.D;
+    const long long np = oracle_param_count(hdr);
+    /* offsets of the parameter groups in the block */
+    const size_t oB = 0, oW1 = (M.enc == ORACLE_ENC_FOURIER) ? (size_t)M.m * 3 : 0;
+    const size_t ob1 = oW1 + (size_t)W * D, oWh = ob1 + W, obh = oWh + (size_t)(L - 1) * W * W;
+    const size_t otw = obh + (size_t)(L - 1) * W, otb = otw + (size_t)L * 2 * W;
+    (void)oB;
+    int nt = 1;
+#ifdef _OPENMP
+    nt = omp_get_max_threads();
+#endif
+    double *acc = (double *)calloc((size_t)nt * (size_t)np, sizeof(double));
+    double *lacc = (double *)calloc((size_t)nt, sizeof(double));
+    if (!acc || !lacc) { free(acc); free(lacc); return -2; }
+    int bad = 0;
+    #pragma omp parallel num_threads(nt)
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *G = acc + (size_t)tid * (size_t)np;
+        double *h0 = (double *)malloc(sizeof(double) * D);
+        double *U = (double *)malloc(sizeof(double) * (size_t)L * W);
+        double *H = (double *)malloc(sizeof(double) * (size_t)L * W);
+        double *TA = (double *)malloc(sizeof(double) * L);
+        double *TB = (double *)malloc(sizeof(double) * L);
+        double *Y = (double *)malloc(sizeof(double) * L);
+        double *Gt = (double *)malloc(sizeof(double) * L);
+        double *g = (double *)malloc(sizeof(double) * W);
+        double *dl = (double *)malloc(sizeof(double) * W);
+        if (!h0 || !U || !H || !TA || !TB || !Y || !Gt || !g || !dl) bad = 1;
+        #pragma omp for schedule(static)
+        for (int64_t i = 0; i < n; ++i) {
+            if (bad) continue;
+            features(&M, pts + 3 * i, h0, NULL);
+            double y = 0.0;
+            for (int l = 1; l <= L; ++l) {
+                const double *hp = (l == 1) ? h0 : H + (size_t)(l - 2) * W;
+                const int fan = (l == 1) ? D : W;
+                const float *Wl = (l == 1) ? M.W1 : M.Wh + (size_t)(l - 2) * W * W;
+                const float *bl = (l == 1) ? M.b1 : M.bh + (size_t)(l - 2) * W;
+                double *u = U + (size_t)(l - 1) * W, *h = H + (size_t)(l - 1) * W;
+                for (int j = 0; j < W; ++j) {
+                    u[j] = dot_f(Wl + (size_t)j * fan, hp, fan) + (double)bl[j];
+                    h[j] = act_value(&M, u[j]);
+                }
+                const float *a = M.tw + (size_t)(l - 1) * 2 * W, *b = a + W;
+                TA[l - 1] = dot_f(a, h, W) + (double)M.tb[(l - 1) * 2];
+                TB[l - 1] = (M.tail_kind == ORACLE_TAIL_MULT && l >= 2) ? dot_f(b, h, W) + (double)M.tb[(l - 1) * 2 + 1] : 1.0;
+                y += TA[l - 1] * TB[l - 1];
+                Y[l - 1] = y;
+            }
+            const double target = (double)gt[i];
+            double s = 0.0;
+            for (int l = L; l >= 1; --l) {
+                const double r = Y[l - 1] - target;
+                lacc[tid] += fabs(r);
+                s += (r > 0.0 ? 1.0 : (r < 0.0 ? -1.0 : 0.0)) / (double)n;
+                Gt[l - 1] = s;
+            }
+            for (int j = 0; j < W; ++j) g[j] = 0.0;
+            for (int l = L; l >= 1; --l) {
+                const double *h = H + (size_t)(l - 1) * W, *u = U + (size_t)(l - 1) * W;
+                const float *a = M.tw + (size_t)(l - 1) * 2 * W, *b = a + W;
+                double *da = G + otw + (size_t)(l - 1) * 2 * W, *db = da + W;
+                double *dc = G + otb + (size_t)(l - 1) * 2;
+                const double Gl = Gt[l - 1];
+                if (M.tail_kind == ORACLE_TAIL_MULT && l >= 2) {
+                    for (int j = 0; j < W; ++j) {
+                        da[j] += Gl * TB[l - 1] * h[j];
+                        db[j] += Gl * TA[l - 1] * h[j];
+                        g[j] += Gl * (TB[l - 1] * (double)a[j] + TA[l - 1] * (double)b[j]);
+                    }
+                    dc[0] += Gl * TB[l - 1];
+                    dc[1] += Gl * TA[l - 1];
+                } else {
+                    for (int j = 0; j < W; ++j) {
+                        da[j] += Gl * h[j];
+                        g[j] += Gl * (double)a[j];
+                    }
+                    dc[0] += Gl;
+                }
+                for (int j = 0; j < W; ++j) dl[j] = g[j] * act_slope(&M, u[j]);
+                const int fan = (l == 1) ? D : W;
+                const double *hp = (l == 1) ? h0 : H + (size_t)(l - 2) * W;
+                const float *Wl = (l == 1) ? M.W1 : M.Wh + (size_t)(l - 2) * W * W;
+                double *dW = G + ((l == 1) ? oW1 : oWh + (size_t)(l - 2) * W * W);
+                double *dbias = G + ((l == 1) ? ob1 : obh + (size_t)(l - 2) * W);
+                for (int j = 0; j < W; ++j) {
+                    dbias[j] += dl[j];
+                    for (int k = 0; k < fan; ++k) dW[(size_t)j * fan + k] += dl[j] * hp[k];
+                }
+                if (l > 1) {
+                    for (int k = 0; k < W; ++k) {
+                        double t = 0.0;
+                        for (int j = 0; j < W; ++j) t += (double)Wl[(size_t)j * W + k] * dl[j];
+                        g[k] = t;
+                    }
+                }
+            }
+        }
+        free(h0); free(U); free(H); free(TA); free(TB); free(Y); free(Gt); free(g); free(dl);
+    }
+    if (!bad) {
+        double ls = 0.0;
+        for (int t = 0; t < nt; ++t) ls += lacc[t];
+        *loss = ls / (double)n;
+        for (long long k = 0; k < np; ++k) {
+            double s = 0.0;
+            for (int t = 0; t < nt; ++t) s += acc[(size_t)t * (size_t)np + (size_t)k];
+            grad[k] = s;
+        }
+    }
+    free(acc);
+    free(lacc);
+    return bad ? -2 : 0;
+}
