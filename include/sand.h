@@ -334,6 +334,46 @@ sand_status sand_server_destroy(sand_server s);
 typedef enum { SAND_PROBE_FFMA = 0, SAND_PROBE_SIN = 1 } sand_probe_kind;
 sand_status sand_probe_rate(int kind, int device, int n_blocks, int iters, float *d_sink, void *stream);
 
+/* ---------------------------------------------------------------- training
+ * T-MLP training steps (Sec. 3.3): the loss is Eq. 4 with the L1 SDF loss of Eq. 8,
+ *     L = sum_{i=1..L} (1/n) sum_x | y_i(x) - y_gt(x) |,
+ * summed over every tail, so every hidden layer is supervised; the optimiser is Adam (Sec. 4.1:
+ * learning rate 1e-4).  |r|' is taken as sign(r) with sign(0) = 0.  A trainer owns a float32
+ * master copy of the model's parameters (in the parameter-block order of sand_load_tmlp_mem),
+ * Adam's two moments, and device buffers for batches of up to max_points points; the model it
+ * was made from is not changed until sand_trainer_commit.
+ * The hidden-layer products of the forward pass, of the backward pass (dL/dh_{l-1} = W_l^T
+ * delta_l) and of the weight gradients (dL/dW_l = sum_x delta_l h_{l-1}^T) run on the tcgen05
+ * tensor cores with float32-class accuracy (each operand split into two fp16 terms, three
+ * products, float32 accumulation), everything else in float32 on the CUDA cores.  Supported:
+ * raw-coordinate models (no Fourier encoder) of width 64, 128 or 256, every activation and
+ * tail kind; else SAND_EUNSUPPORTED.  Calls on one trainer must be stream-ordered. */
+typedef struct sand_trainer_s *sand_trainer;
+typedef struct {
+    int64_t max_points;  /* largest batch (default 2^17) */
+    float lr;            /* Adam step size (default 1e-4) */
+    float beta1, beta2;  /* Adam decay rates (defaults 0.9, 0.999) */
+    float eps;           /* Adam epsilon (default 1e-8) */
+    int32_t reserved;
+} sand_train_opts;
+sand_status sand_trainer_create(sand_model m, const sand_train_opts *opts, sand_trainer *out);
+/* One step on a batch: d_points device float32 [n][3], d_targets device float32 [n] (y_gt), 1 <= n
+ * <= max_points.  Computes the loss and the gradient of every parameter; with update != 0 then
+ * applies one Adam step.  d_loss (device float32 [1], nullable) receives L; d_grad (device float32
+ * [n_params], nullable) receives dL/dparams in the parameter-block order (a Fourier matrix would
+ * get 0).  Stream-ordered and asynchronous. */
+sand_status sand_train_step(sand_trainer t, const float *d_points, const float *d_targets, int64_t n, float *d_loss,
+                            float *d_grad, int update, void *stream);
+/* The trainer's current parameters (host float32 [n_params], parameter-block order); synchronous. */
+sand_status sand_trainer_params(sand_trainer t, float *h_params, size_t n_params);
+/* Copy the trainer's parameters into its model (its packed weights are rebuilt on the next query);
+ * synchronous. */
+sand_status sand_trainer_commit(sand_trainer t);
+/* SAND_ETIMEOUT if a bounded device-side wait of a training kernel gave up since the trainer was
+ * made (synchronises the stream), else SAND_OK. */
+sand_status sand_trainer_status(sand_trainer t, void *stream);
+sand_status sand_trainer_destroy(sand_trainer t);
+
 /* Describe a loaded model. */
 sand_status sand_model_desc(sand_model m, sand_tmlp_desc *out);
 

@@ -73,6 +73,11 @@ class MapBuildOpts(ctypes.Structure):
                 ("precision", ctypes.c_int32)]
 
 
+class TrainOpts(ctypes.Structure):
+    _fields_ = [("max_points", ctypes.c_int64), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("reserved", ctypes.c_int32)]
+
+
 class QueryStats(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_uint32), ("n_network", ctypes.c_uint32), ("count", ctypes.c_uint32 * 16)]
 
@@ -83,7 +88,8 @@ EXPORTS = ("sand_load_tmlp", "sand_load_tmlp_mem", "sand_load_depth_map", "sand_
            "sand_read_stats", "sand_model_desc", "sand_free", "sand_last_error", "sand_server_create",
            "sand_server_submit", "sand_server_wait", "sand_server_stats", "sand_server_destroy",
            "sand_trace_state_bytes", "sand_sphere_trace", "sand_build_depth_map", "sand_query_sdf_dynamic",
-           "sand_probe_rate")
+           "sand_probe_rate", "sand_query_sdf_noalloc", "sand_trainer_create", "sand_train_step",
+           "sand_trainer_params", "sand_trainer_commit", "sand_trainer_status", "sand_trainer_destroy")
 
 
 def lib() -> ctypes.CDLL:
@@ -121,6 +127,13 @@ def lib() -> ctypes.CDLL:
     L.sand_build_depth_map.argtypes = [P, ctypes.POINTER(DepthMapDesc), P, P, ctypes.POINTER(MapBuildOpts), P, P]
     L.sand_query_sdf_dynamic.argtypes = [P, P, I64, ctypes.c_float, P, P, ctypes.POINTER(QueryOpts), P]
     L.sand_probe_rate.argtypes = [I32, I32, I32, I32, P, P]
+    L.sand_query_sdf_noalloc.argtypes = [P, P, I64, P, ctypes.POINTER(QueryOpts), P]
+    L.sand_trainer_create.argtypes = [P, ctypes.POINTER(TrainOpts), ctypes.POINTER(P)]
+    L.sand_train_step.argtypes = [P, P, P, I64, P, P, I32, P]
+    L.sand_trainer_params.argtypes = [P, P, ctypes.c_size_t]
+    L.sand_trainer_commit.argtypes = [P]
+    L.sand_trainer_status.argtypes = [P, P]
+    L.sand_trainer_destroy.argtypes = [P]
     for name in EXPORTS:
         if name not in ("sand_workspace_bytes", "sand_last_error", "sand_trace_state_bytes"):
             getattr(L, name).restype = ctypes.c_int
@@ -451,6 +464,59 @@ class Server:
     def close(self):
         if self._h:
             lib().sand_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Trainer:
+    """T-MLP training (Sec. 3.3): the loss over every tail (Eq. 4 / Eq. 8) and Adam, on a model's
+    float32 master copy (sand_trainer_*).  step() takes device points [n, 3] and targets [n]."""
+
+    def __init__(self, model: Model, max_points: int = 1 << 17, lr: float = 1e-4, beta1: float = 0.9,
+                 beta2: float = 0.999, eps: float = 1e-8):
+        self.model = model
+        o = TrainOpts(int(max_points), float(lr), float(beta1), float(beta2), float(eps), 0)
+        h = ctypes.c_void_p()
+        _check(lib().sand_trainer_create(model._h, ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        d = model.desc
+        L, W, D = d.n_layers, d.width, d.in_dim
+        self.n_params = W * D + W + (L - 1) * W * W + (L - 1) * W + L * 2 * W + L * 2
+
+    def step(self, points: torch.Tensor, targets: torch.Tensor, update: bool = True, loss: Optional[torch.Tensor] = None,
+             grad: Optional[torch.Tensor] = None, stream: Optional[torch.cuda.Stream] = None):
+        """One training step; returns (loss [1], grad [n_params] or None) as device tensors."""
+        pts = _as_points(points, self.model.device)
+        t = targets.contiguous()
+        if t.dtype != torch.float32 or t.numel() != pts.shape[0] or t.device != pts.device:
+            raise ValueError("targets: float32 [n] on the points' device")
+        if loss is None:
+            loss = torch.empty(1, dtype=torch.float32, device=pts.device)
+        gp = grad.data_ptr() if grad is not None else None
+        _check(lib().sand_train_step(self._h, ctypes.c_void_p(pts.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                     pts.shape[0], ctypes.c_void_p(loss.data_ptr()), ctypes.c_void_p(gp) if gp else None,
+                                     int(bool(update)), _stream_handle(stream)))
+        return loss, grad
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.n_params, np.float32)
+        _check(lib().sand_trainer_params(self._h, out.ctypes.data_as(ctypes.c_void_p), out.size))
+        return out
+
+    def commit(self) -> None:
+        _check(lib().sand_trainer_commit(self._h))
+
+    def status(self, stream: Optional[torch.cuda.Stream] = None) -> None:
+        _check(lib().sand_trainer_status(self._h, _stream_handle(stream)))
+
+    def close(self) -> None:
+        if self._h:
+            lib().sand_trainer_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -475,6 +475,20 @@ sand_status model_eval_all_tails(sand_model m, const float *d_pts, int64_t n, fl
     return SAND_OK;
 }
 
+const sand_tmlp_desc &model_desc_ref(sand_model m) { return m->desc; }
+const float *model_params(sand_model m) { return m->params.data(); }
+size_t model_param_count(sand_model m) { return m->params.size(); }
+
+sand_status model_replace_params(sand_model m, const float *h_params) {
+    DeviceGuard g(m->device);
+    SAND_CUDA(cudaDeviceSynchronize(), "device synchronize");
+    memcpy(m->params.data(), h_params, m->params.size() * sizeof(float));
+    cudaFree(m->d_simt);
+    m->d_simt = nullptr;
+    tc_release(&m->tc);
+    return pack_simt(m);
+}
+
 sand_status model_trace_buffer(sand_model m, size_t bytes, void **out) {
     if (m->trace_bytes < bytes) {
         cudaFree(m->d_trace);

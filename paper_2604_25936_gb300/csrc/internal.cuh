@@ -146,5 +146,12 @@ sand_status model_eval_all_tails(sand_model m, const float *d_pts, int64_t n, fl
 int model_layers(sand_model m);
 // Grow-only device buffer owned by the model for the sphere tracer (stream-ordered reuse).
 sand_status model_trace_buffer(sand_model m, size_t bytes, void **out);
+// The model's shape, host copy of its float32 parameter block and device.
+const sand_tmlp_desc &model_desc_ref(sand_model m);
+const float *model_params(sand_model m);
+size_t model_param_count(sand_model m);
+// Replace the parameter block (same shape): the CUDA-core weights are re-uploaded and the packed
+// tensor-core weights dropped (rebuilt by the next tensor-core query).  Synchronises the device.
+sand_status model_replace_params(sand_model m, const float *h_params);
 
 }  // namespace sand

@@ -64,6 +64,19 @@ def test_server_handles(B):
     assert L.sand_server_destroy(None) == B.SAND_OK
 
 
+def test_trainer_entry_points_refuse_null(B):
+    L = B.lib()
+    P = ctypes.c_void_p
+    h = P()
+    buf = P(256)
+    _einval(B, L.sand_trainer_create(None, None, ctypes.byref(h)))
+    _einval(B, L.sand_train_step(None, buf, buf, 10, None, None, 1, None))
+    _einval(B, L.sand_trainer_params(None, buf, 10))
+    _einval(B, L.sand_trainer_commit(None))
+    _einval(B, L.sand_trainer_status(None, None))
+    assert L.sand_trainer_destroy(None) == B.SAND_OK
+
+
 def test_sizes_without_a_device(B):
     L = B.lib()
     # workspace: a 1 KiB header, per-block histograms, then 17 B per point (exit byte, float4 row)
