@@ -384,6 +384,51 @@ def serve_bench(sand, models, precision, pool, run_s: float, sweep_s: float, mem
     return out
 
 
+def train_bench(sand, local: int, steps: int, n: int = 100000):
+    """Training steps of the benchmark's 8 x 256 SIREN T-MLP (Sec. 3.3: the loss of Eq. 4 / Eq. 8
+    over every tail, its gradient, one Adam update) on a batch of n points sampled as Sec. 4.1
+    describes (60 % on the analytic scene's surface, 40 % moved by Gaussian noise of sigma 0.01)
+    with their exact SDF as targets.  Algorithmic work per step: the forward pass
+    (2*3*W + (L-1)*2*W^2 + L*2*W per point), the backward products W_l^T delta_l and the weight
+    gradients delta_l h_{l-1}^T ((L-1)*2*W^2 each per point, plus 2*3*W for W_1)."""
+    import torch
+    from paper_2604_25936_gb300.binding import Trainer
+    model = synth.siren_tmlp(N_LAYERS, WIDTH, seed=SEED)
+    pts, gt = synth.training_batch(n, seed=21)
+    m = sand.Model.from_params(*model.header_ints(), model.omega0, model.flat(), device=local)
+    tr = Trainer(m, max_points=n)
+    x, t = torch.from_numpy(pts).cuda(), torch.from_numpy(gt).cuda()
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        tr.step(x, t, loss=loss)
+    torch.cuda.synchronize()
+    first = float(loss.item())
+    stream = torch.cuda.current_stream()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        tr.step(x, t, loss=loss)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    tr.status()
+    ms = t0.elapsed_time(t1) / steps
+    L, W = N_LAYERS, WIDTH
+    fwd = 2 * 3 * W + (L - 1) * 2 * W * W + L * 2 * W
+    flops = float(n) * (fwd + 2 * (L - 1) * 2 * W * W + 2 * 3 * W)
+    pk, pk_src = peaks()
+    peak = pk.get("bf16_tflops_sustained", 1700.0) / 3.0
+    achieved = flops / (ms / 1e3) / 1e12
+    out = {"model": "8x256 SIREN, linear tails", "batch_points": n, "sampling": "60% surface, 40% surface + N(0, 0.01^2)",
+           "ms_per_step": ms, "steps_per_s": 1e3 / ms, "points_per_s": n / (ms / 1e3),
+           "loss_after_warmup": first, "loss_after_timed": float(loss.item()),
+           "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                        "peak_source": "%s bf16 sustained / 3 (float32 split products)" % pk_src},
+           "paper_context": "Table 9: 0.0241 s per T-MLP training iteration (SIREN 8x256, RTX 4090, PyTorch, batch not stated)"}
+    tr.close()
+    m.free()
+    return out
+
+
 def paper_variants(sand, local: int, steps: int, prec: str, peak_tflops: float, hbm_gbs: float):
     """The benchmark lattice query as the paper states the method: (a) multiplicative tails for
     layers >= 2 (Eq. 3), and (b) the far-field depth map, whose leaves away from the surface
@@ -419,6 +464,7 @@ def paper_variants(sand, local: int, steps: int, prec: str, peak_tflops: float, 
         torch.cuda.synchronize()
         step_ms = t0.elapsed_time(t1) / steps
         mlp_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / steps
+        pre_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / steps
         flops = float((flops_per_point(np.arange(N_LAYERS + 1), WIDTH, tail == synth.TAIL_MULT) * counts).sum())
         achieved = flops / (mlp_ms / 1e3) / 1e12
         y_ref = oracle.query(model, tree, pts[idx])
@@ -428,10 +474,19 @@ def paper_variants(sand, local: int, steps: int, prec: str, peak_tflops: float, 
                  "max_abs_err_vs_oracle_20k": float(np.abs(out.cpu().numpy()[idx].astype(np.float64) - y_ref).max()),
                  "exit_layer_histogram": {str(d): int(c) for d, c in enumerate(counts)}}
         if far:
-            gbs = 16.0 * n / (step_ms / 1e3) / 1e9
-            entry["far_points"] = int(counts[0])
-            entry["hbm"] = {"bytes_per_point": 16, "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s",
-                            "frac": gbs / hbm_gbs}
+            # the memory-bound stages: the lookup reads a point and writes its exit byte (far points
+            # also their stored value); the scatter reads every exit byte and copies the network
+            # points into sorted 16-byte rows
+            n_far = int(counts[0])
+            n_net = n - n_far
+            bytes_ = 14.0 * n + 4.0 * n_far + 28.0 * n_net
+            gbs = bytes_ / (pre_ms / 1e3) / 1e9
+            entry["far_points"] = n_far
+            entry["lookup_bin_ms"] = pre_ms
+            entry["hbm"] = {"kernels": "lookup_kernel + scan_kernel + scatter_kernel", "bytes": bytes_,
+                            "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s", "frac": gbs / hbm_gbs,
+                            "algorithmic_bytes_per_point": 16,
+                            "step_achieved_of_algorithmic": 16.0 * n / (step_ms / 1e3) / 1e9}
         res[name] = entry
         m.free()
     return res
@@ -754,6 +809,7 @@ def main():
                          "serving; the float32 runs take a third of it)")
     ap.add_argument("--sweep-seconds", type=float, default=4.0, help="length of each run of the serving load sweep")
     ap.add_argument("--peaks", action="store_true", help="measure GEMM, FMA and sine peaks of this GPU; prints one line")
+    ap.add_argument("--train-only", action="store_true", help="only the training-step measurement; prints one line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -761,6 +817,14 @@ def main():
         return run_peaks(args)
     if args.profile:
         return run_profile_case(args)
+    if args.train_only:
+        import torch
+        import paper_2604_25936_gb300 as sand
+        from paper_2604_25936_gb300 import build as sand_build
+        sand_build.build()
+        torch.cuda.set_device(0)
+        print(json.dumps({"training": train_bench(sand, 0, max(3, args.steps))}), flush=True)
+        return 0
 
     import torch
     import torch.distributed as dist
@@ -921,6 +985,10 @@ def main():
     if rank == 0 and not args.no_variants:
         variant = precision_variant(sand, local, max(3, K // 4))
 
+    trainb = None
+    if rank == 0 and not args.no_variants:
+        trainb = train_bench(sand, local, max(3, K // 2))
+
     paperv = None
     if rank == 0 and not args.no_variants and prec != "fp32_simt":
         paperv = paper_variants(sand, local, max(3, K // 4), prec, roof["peak"], pk.get("hbm_gbs", 6800.0))
@@ -963,6 +1031,7 @@ def main():
         "serve": serve,
         "precision_variant": variant,
         "paper_variants": paperv,
+        "training": trainb,
         "sphere_trace": tr,
         "depth_map_build": mapb,
         "dynamic_exit": dynb,

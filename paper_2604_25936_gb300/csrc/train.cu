@@ -40,15 +40,18 @@ namespace sand {
 
 enum TrEpi { TR_FWD = 0, TR_BWD = 1, TR_DW = 2 };
 
-constexpr int kTrThreads = 256;            // warp 1: TMEM + MMA issue; the other 7 warps produce operands
-constexpr int kTrProducers = kTrThreads - 32;
+constexpr int kTrProdWarps = 4;           // warps 0..3 produce operands
+constexpr int kTrProducers = 32 * kTrProdWarps;
+constexpr int kTrMmaWarp = 4;             // TMEM owner and MMA issuer
+constexpr int kTrThreads = 32 * 9;        // warps 5..8: epilogue
 constexpr int kTrBM = 128;                 // rows of a tile (MMA M)
 constexpr int kTrMaxStages = 4;
 constexpr int kTrSmem = 227 * 1024;
 
 struct TrGemm {
     int M, N, K;          // output rows (bounds), columns (= MMA N), reduction length
-    int kb_per_split;     // DW: 64-element K-blocks per CTA along grid.y
+    int m_tiles, splits;  // tiles: m_tiles row tiles x splits of the K range
+    int kb_per_split;     // 64-element K-blocks per split
     int act;
     float omega0;
     // A operand: FWD act(a[row][k]); BWD a[row][k]; DW a[k][row]   (ld = a_ld)
@@ -134,6 +137,105 @@ __device__ __forceinline__ bool tr_wait_warp(uint32_t bar, uint32_t parity, vola
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
+// One stage of operands (64 K-elements of a 128-row A tile and an N-row B tile) from global memory
+// into shared memory, split into fp16 hi and lo parts, by the kTrProducers producer threads.
+// Every global load of a group is issued before any of its values is used, so a stage costs a
+// few memory latencies rather than one per chunk.
+template <int EPI>
+__device__ __forceinline__ void tr_produce_stage(const TrGemm &P, int pt, int m0, int k0, uint32_t ahi, uint32_t alo,
+                                                 uint32_t bhi, uint32_t blo) {
+    const int N = P.N;
+    if (EPI != TR_DW) {
+        // A[r][kk] = (act of) a[m0 + r][k0 + kk]: chunk it = (row it / 8, 8 K-elements it % 8), 32
+        // contiguous bytes; eight consecutive threads read one row's 256 bytes
+        constexpr int NA = kTrBM * 8 / kTrProducers;
+        float4 va[NA][2];
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+            const int it = pt + j * kTrProducers;
+            const int row = m0 + (it >> 3), kk = k0 + 8 * (it & 7);
+            const bool in = row < P.M && kk + 8 <= P.K;
+            const float4 *src = reinterpret_cast<const float4 *>(P.a + (size_t)row * P.a_ld + kk);
+            va[j][0] = in ? __ldg(src) : make_float4(0.f, 0.f, 0.f, 0.f);
+            va[j][1] = in ? __ldg(src + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        // B: the packed fp16 weights (L2-resident), 16-byte asynchronous copies into the swizzled slots
+        for (int it = pt; it < N * 8; it += kTrProducers) {
+            const int r = it >> 3, c = it & 7;
+            cp_async16(bhi + tr_swz(r, c), P.bp + (size_t)r * P.bp_ld + k0 + 8 * c);
+            cp_async16(blo + tr_swz(r, c), P.bp + ((size_t)N + r) * P.bp_ld + k0 + 8 * c);
+        }
+        cp_async_commit();
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+            const int it = pt + j * kTrProducers;
+            float v[8] = {va[j][0].x, va[j][0].y, va[j][0].z, va[j][0].w, va[j][1].x, va[j][1].y, va[j][1].z, va[j][1].w};
+            if (EPI == TR_FWD) {  // act(0) = 0 for every activation: padding stays 0
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[e] = tr_act(P.act, v[e], P.omega0);
+            }
+            uint4 hi, lo;
+            tr_split8(v, hi, lo);
+            st_shared_v4(ahi + tr_swz(it >> 3, it & 7), hi);
+            st_shared_v4(alo + tr_swz(it >> 3, it & 7), lo);
+        }
+        cp_async_wait_all();
+    } else {
+        // Both operands are [k][row] in memory (rows contiguous).  A quad is four consecutive rows
+        // of one chunk: eight float4 loads along the rows, one per K-element, give four chunks.
+        // Consecutive threads take consecutive quads of the same chunk column.
+        // A[r][kk] = delta'[k0 + kk][m0 + r]: 32 quads per chunk column, 256 in all
+        constexpr int NQ = 2;  // quads per thread per group
+        for (int g0 = 0; g0 < kTrBM * 2 + N * 2; g0 += NQ * kTrProducers) {
+            const bool is_a = g0 < kTrBM * 2;  // groups never straddle A and B (both are multiples)
+            float4 vq[NQ][8];
+#pragma unroll
+            for (int j = 0; j < NQ; ++j) {
+                const int q = g0 + pt + j * kTrProducers - (is_a ? 0 : kTrBM * 2);
+                const int nq = is_a ? 32 : (N >> 2);
+                const int q4 = q % nq, c = q / nq;
+                const int row0 = (is_a ? m0 : 0) + 4 * q4;
+                const bool in = q < (is_a ? kTrBM * 2 : N * 2) && (!is_a || row0 + 4 <= P.M);
+                const float *base = is_a ? P.a : P.b;
+                const int ld = is_a ? P.a_ld : P.b_ld;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int kk = k0 + 8 * c + e;
+                    vq[j][e] = (in && kk < P.K) ? __ldg(reinterpret_cast<const float4 *>(base + (size_t)kk * ld + row0))
+                                                : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < NQ; ++j) {
+                const int q = g0 + pt + j * kTrProducers - (is_a ? 0 : kTrBM * 2);
+                if (q >= (is_a ? kTrBM * 2 : N * 2)) continue;
+                const int nq = is_a ? 32 : (N >> 2);
+                const int q4 = q % nq, c = q / nq;
+                const uint32_t dhi = is_a ? ahi : bhi, dlo = is_a ? alo : blo;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    float v[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const float x = i == 0 ? vq[j][e].x : i == 1 ? vq[j][e].y : i == 2 ? vq[j][e].z : vq[j][e].w;
+                        v[e] = is_a ? x : tr_act(P.act, x, P.omega0);  // B = act(z_{l-1})
+                    }
+                    uint4 hi, lo;
+                    tr_split8(v, hi, lo);
+                    st_shared_v4(dhi + tr_swz(4 * q4 + i, c), hi);
+                    st_shared_v4(dlo + tr_swz(4 * q4 + i, c), lo);
+                }
+            }
+        }
+    }
+}
+
+// Persistent GEMM: CTA b takes tiles b, b + grid, ...; tile t is rows 128 (t % m_tiles) .. + 127
+// and K-blocks of split t / m_tiles.  Two accumulators in TMEM let the epilogue of one tile run
+// while the MMAs of the next one do.
+//   warps 0..3  producers (operands into the shared-memory stage ring)
+//   warp 4      TMEM owner, MMA issuer (one thread)
+//   warps 5..8  epilogue: thread (quadrant warp & 3, lane i) owns tile row 32 (warp & 3) + i
 template <int EPI>
 __global__ void __launch_bounds__(kTrThreads, 1) tr_gemm_kernel(const TrGemm P) {
     extern __shared__ uint8_t smem_raw[];
@@ -141,32 +243,39 @@ __global__ void __launch_bounds__(kTrThreads, 1) tr_gemm_kernel(const TrGemm P) 
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)P.n_stages * P.stage_bytes);
     uint64_t *full = bars;                       // [stage]: operands written (kTrProducers arrivals)
     uint64_t *empty = bars + kTrMaxStages;       // [stage]: the stage's MMAs completed (commit)
-    uint64_t *dfull = bars + 2 * kTrMaxStages;   // the accumulator is complete (commit)
-    uint64_t *drain = dfull + 1;
+    uint64_t *acc_full = bars + 2 * kTrMaxStages;   // [2]: an accumulator is complete (commit)
+    uint64_t *acc_empty = acc_full + 2;             // [2]: ... and read out (4 epilogue warps)
+    uint64_t *drain = acc_empty + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
     volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int N = P.N;
     const uint32_t a_bytes = kTrBM * 128, b_bytes = (uint32_t)N * 128;
-    const int m0 = blockIdx.x * kTrBM;
     const int kb_all = (P.K + 63) / 64;
-    const int kb0 = EPI == TR_DW ? blockIdx.y * P.kb_per_split : 0;
-    const int kb1 = EPI == TR_DW ? min(kb_all, kb0 + P.kb_per_split) : kb_all;
-    const int n_kb = max(0, kb1 - kb0);
+    const int n_tiles = P.m_tiles * P.splits;
     uint32_t tcols = 32;
-    while (tcols < (uint32_t)N) tcols <<= 1;
+    while (tcols < 2u * (uint32_t)N) tcols <<= 1;
+    auto tile_kb = [&](int t, int &m0, int &kb0, int &kb1) {
+        m0 = (t % P.m_tiles) * kTrBM;
+        const int sp = t / P.m_tiles;
+        kb0 = sp * P.kb_per_split;
+        kb1 = min(kb_all, kb0 + P.kb_per_split);
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < P.n_stages; ++s) {
             mbar_init(smem_u32(&full[s]), kTrProducers);
             mbar_init(smem_u32(&empty[s]), 1);
         }
-        mbar_init(smem_u32(dfull), 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&acc_full[b]), 1);
+            mbar_init(smem_u32(&acc_empty[b]), 4);
+        }
         mbar_init(smem_u32(drain), 1);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) {
+    if (warp == kTrMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(tcols)
                      : "memory");
@@ -177,45 +286,77 @@ __global__ void __launch_bounds__(kTrThreads, 1) tr_gemm_kernel(const TrGemm P) 
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 1) {
+    if (warp < kTrProdWarps) {
+        // ------------------------------------------------ producers
+        const int pt = threadIdx.x;
+        uint32_t it = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+            int m0, kb0, kb1;
+            tile_kb(t, m0, kb0, kb1);
+            for (int kb = kb0; kb < kb1 && ok; ++kb, ++it) {
+                const uint32_t s = it % (uint32_t)P.n_stages, round = it / (uint32_t)P.n_stages;
+                if (round > 0) {
+                    ok = tr_wait_warp(smem_u32(&empty[s]), (round - 1) & 1u, abort, P.status);
+                    if (!ok) break;
+                }
+                const uint32_t st = smem_u32(smem + (size_t)s * P.stage_bytes);
+                tr_produce_stage<EPI>(P, pt, m0, kb * 64, st, st + a_bytes, st + 2 * a_bytes, st + 2 * a_bytes + b_bytes);
+                fence_async_smem();  // generic-proxy writes -> visible to the tensor core's async proxy
+                mbar_arrive(smem_u32(&full[s]));
+            }
+        }
+    } else if (warp == kTrMmaWarp) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t idesc = (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTrBM >> 4) << 24);
             bool ok = true;
-            uint32_t acc = 0;
-            for (int i = 0; i < n_kb && ok; ++i) {
-                const int s = i % P.n_stages;
-                const uint32_t ph = (uint32_t)(i / P.n_stages) & 1u;
-                if (!mbar_try(smem_u32(&full[s]), ph)) {
-                    const uint64_t t0 = globaltimer();
-                    while (!mbar_try(smem_u32(&full[s]), ph)) {
-                        if (*abort) { ok = false; break; }
-                        if (globaltimer() - t0 > kTimeoutNs) {
-                            *abort = 1;
-                            atomicOr(P.status, 1u);
-                            ok = false;
-                            break;
-                        }
+            uint32_t it = 0, ti = 0;
+            auto wait = [&](uint32_t bar, uint32_t parity) {
+                if (mbar_try(bar, parity)) return true;
+                const uint64_t t0 = globaltimer();
+                while (!mbar_try(bar, parity)) {
+                    if (*abort) return false;
+                    if (globaltimer() - t0 > kTimeoutNs) {
+                        *abort = 1;
+                        atomicOr(P.status, 1u);
+                        return false;
                     }
                 }
-                if (!ok) break;
-                tc_fence_after();
-                const uint32_t st = smem_u32(smem + (size_t)s * P.stage_bytes);
-                const uint32_t ahi = st, alo = st + a_bytes, bhi = st + 2 * a_bytes, blo = bhi + b_bytes;
-                const int ksteps = min(4, (P.K - (kb0 + i) * 64 + 15) / 16);
-                for (int k = 0; k < ksteps; ++k) {
-                    const uint64_t dah = smem_desc(ahi + 32 * k), dal = smem_desc(alo + 32 * k);
-                    const uint64_t dbh = smem_desc(bhi + 32 * k), dbl = smem_desc(blo + 32 * k);
-                    mma_f16(tmem, dah, dbh, idesc, acc);
-                    mma_f16(tmem, dal, dbh, idesc, 1u);
-                    mma_f16(tmem, dah, dbl, idesc, 1u);
-                    acc = 1u;
+                return true;
+            };
+            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++ti) {
+                int m0, kb0, kb1;
+                tile_kb(t, m0, kb0, kb1);
+                const uint32_t b = ti & 1u, use = ti >> 1;
+                if (use > 0) {
+                    ok = wait(smem_u32(&acc_empty[b]), (use - 1) & 1u);
+                    if (!ok) break;
+                    tc_fence_after();
                 }
-                mma_commit(smem_u32(&empty[s]));
+                const uint32_t d = tmem + b * (uint32_t)N;
+                uint32_t acc = 0;
+                for (int kb = kb0; kb < kb1 && ok; ++kb, ++it) {
+                    const uint32_t s = it % (uint32_t)P.n_stages, round = it / (uint32_t)P.n_stages;
+                    ok = wait(smem_u32(&full[s]), round & 1u);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t st = smem_u32(smem + (size_t)s * P.stage_bytes);
+                    const uint32_t ahi = st, alo = st + a_bytes, bhi = st + 2 * a_bytes, blo = bhi + b_bytes;
+                    const int ksteps = min(4, (P.K - kb * 64 + 15) / 16);
+                    for (int k = 0; k < ksteps; ++k) {
+                        const uint64_t dah = smem_desc(ahi + 32 * k), dal = smem_desc(alo + 32 * k);
+                        const uint64_t dbh = smem_desc(bhi + 32 * k), dbl = smem_desc(blo + 32 * k);
+                        mma_f16(d, dah, dbh, idesc, acc);
+                        mma_f16(d, dal, dbh, idesc, 1u);
+                        mma_f16(d, dah, dbl, idesc, 1u);
+                        acc = 1u;
+                    }
+                    mma_commit(smem_u32(&empty[s]));
+                }
+                if (ok) mma_commit(smem_u32(&acc_full[b]));
             }
-            if (ok) {
-                mma_commit(smem_u32(dfull));
-            } else {  // let every issued MMA finish before TMEM is released
+            if (!ok) {  // let every issued MMA finish before TMEM is released
                 mma_commit(smem_u32(drain));
                 const uint64_t t0 = globaltimer();
                 while (!mbar_try(smem_u32(drain), 0) && globaltimer() - t0 < kTimeoutNs) {
@@ -224,163 +365,108 @@ __global__ void __launch_bounds__(kTrThreads, 1) tr_gemm_kernel(const TrGemm P) 
         }
         __syncwarp();
     } else {
-        // ------------------------------------------------ producers (warps 0, 2..7)
-        const int pt = warp == 0 ? lane : threadIdx.x - 32;  // 0 .. kTrProducers - 1
+        // ------------------------------------------------ epilogue
+        const int q = warp & 3;
+        const int r = q * 32 + lane;
         bool ok = true;
-        for (int i = 0; i < n_kb && ok; ++i) {
-            const int s = i % P.n_stages;
-            const uint32_t ph = (uint32_t)(i / P.n_stages) & 1u;
-            if (i >= P.n_stages) {
-                ok = tr_wait_warp(smem_u32(&empty[s]), ph ^ 1u, abort, P.status);
-                if (!ok) break;
+        uint32_t ti = 0;
+        const float inv_s = EPI == TR_DW ? 1.f : __ldg(P.inv_s);
+        for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++ti) {
+            int m0, kb0, kb1;
+            tile_kb(t, m0, kb0, kb1);
+            const uint32_t b = ti & 1u, use = ti >> 1;
+            ok = tr_wait_warp(smem_u32(&acc_full[b]), use & 1u, abort, P.status);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t t_lane = tmem + b * (uint32_t)N + ((uint32_t)(q * 32) << 16);
+            const int row = m0 + r;
+            const bool live = row < P.M;
+            const int split = t / P.m_tiles;
+            float sa = 0.f, sb = 0.f;
+            float gl = 0.f, tav = 0.f, tbv = 0.f;
+            if (EPI == TR_BWD && live) {
+                gl = __ldg(P.g_prev + row);
+                tav = __ldg(P.ta_prev + row);
+                tbv = __ldg(P.tb_prev + row);
             }
-            const int k0 = (kb0 + i) * 64;
-            const uint32_t st = smem_u32(smem + (size_t)s * P.stage_bytes);
-            const uint32_t ahi = st, alo = st + a_bytes, bhi = st + 2 * a_bytes, blo = bhi + b_bytes;
-            // A operand: 128 rows x 8 chunks
-            for (int it = pt; it < kTrBM * 8; it += kTrProducers) {
-                float v[8];
-                int r, c;
-                if (EPI == TR_DW) {  // A[r][kk] = delta'[k0 + kk][m0 + r]: consecutive threads, consecutive rows
-                    r = it % kTrBM;
-                    c = it / kTrBM;
-                    const int row = m0 + r;
+            // BWD: z_{l-1} of the row, one 32-column chunk ahead of its use
+            float4 zc[8], zn[8];
+            if (EPI == TR_BWD) {
+                const float4 *zp = reinterpret_cast<const float4 *>(P.z_prev + (size_t)(live ? row : 0) * N);
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const int kk = k0 + 8 * c + e;
-                        v[e] = (row < P.M && kk < P.K) ? __ldg(P.a + (size_t)kk * P.a_ld + row) : 0.f;
-                    }
-                } else {  // A[r][kk] = (act of) a[m0 + r][k0 + kk]: 32 contiguous bytes per chunk
-                    r = it >> 3;
-                    c = it & 7;
-                    const int row = m0 + r, kk = k0 + 8 * c;
-                    if (row < P.M && kk + 8 <= P.K) {
-                        const float4 *src = reinterpret_cast<const float4 *>(P.a + (size_t)row * P.a_ld + kk);
-                        const float4 x0 = __ldg(src), x1 = __ldg(src + 1);
-                        v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
-                        v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
-                        if (EPI == TR_FWD) {
+                for (int j = 0; j < 8; ++j) zn[j] = __ldg(zp + j);
+            }
+            for (int c0 = 0; c0 < N; c0 += 32) {
+                uint32_t v[32];
+                tmem_ld32(t_lane + (uint32_t)c0, v);
+                if (EPI == TR_BWD) {
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) v[e] = tr_act(P.act, v[e], P.omega0);
-                        }
-                    } else {
+                    for (int j = 0; j < 8; ++j) zc[j] = zn[j];
+                    if (c0 + 32 < N) {
+                        const float4 *zp = reinterpret_cast<const float4 *>(P.z_prev + (size_t)(live ? row : 0) * N + c0 + 32);
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            const bool in = row < P.M && kk + e < P.K;
-                            const float x = in ? __ldg(P.a + (size_t)row * P.a_ld + kk + e) : 0.f;
-                            v[e] = (EPI == TR_FWD && in) ? tr_act(P.act, x, P.omega0) : x;
-                        }
+                        for (int j = 0; j < 8; ++j) zn[j] = __ldg(zp + j);
                     }
                 }
-                uint4 hi, lo;
-                tr_split8(v, hi, lo);
-                st_shared_v4(ahi + tr_swz(r, c), hi);
-                st_shared_v4(alo + tr_swz(r, c), lo);
-            }
-            // B operand: N rows x 8 chunks
-            for (int it = pt; it < N * 8; it += kTrProducers) {
-                if (EPI == TR_DW) {  // B[n][kk] = act(b[k0 + kk][n])
-                    const int r = it % N, c = it / N;
-                    float v[8];
+                tmem_wait_ld();
+                if (!live) continue;
+                if (EPI == TR_DW) {
+                    float4 *dst = reinterpret_cast<float4 *>(P.out + ((size_t)split * P.M + row) * N + c0);
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const int kk = k0 + 8 * c + e;
-                        v[e] = kk < P.K ? tr_act(P.act, __ldg(P.b + (size_t)kk * P.b_ld + r), P.omega0) : 0.f;
+                    for (int j = 0; j < 8; ++j)
+                        dst[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                                             __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
+                } else if (EPI == TR_FWD) {
+                    float4 *dst = reinterpret_cast<float4 *>(P.out + (size_t)row * N + c0);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        float z[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int col = c0 + 4 * j + e;
+                            z[e] = fmaf(__uint_as_float(v[4 * j + e]), inv_s, __ldg(P.bias + col));
+                            const float h = tr_act(P.act, z[e], P.omega0);
+                            sa = fmaf(__ldg(P.tw + col), h, sa);
+                            if (P.mult) sb = fmaf(__ldg(P.tw + N + col), h, sb);
+                        }
+                        dst[j] = make_float4(z[0], z[1], z[2], z[3]);
                     }
-                    uint4 hi, lo;
-                    tr_split8(v, hi, lo);
-                    st_shared_v4(bhi + tr_swz(r, c), hi);
-                    st_shared_v4(blo + tr_swz(r, c), lo);
-                } else {  // packed fp16 rows: copy 16 bytes of hi and of lo (K is a multiple of 64 here)
-                    const int r = it >> 3, c = it & 7;
-                    const uint4 *src_h = reinterpret_cast<const uint4 *>(P.bp + (size_t)r * P.bp_ld + k0 + 8 * c);
-                    const uint4 *src_l =
-                        reinterpret_cast<const uint4 *>(P.bp + ((size_t)N + r) * P.bp_ld + k0 + 8 * c);
-                    st_shared_v4(bhi + tr_swz(r, c), __ldg(src_h));
-                    st_shared_v4(blo + tr_swz(r, c), __ldg(src_l));
+                } else {  // TR_BWD
+                    float4 *dst = reinterpret_cast<float4 *>(P.out + (size_t)row * N + c0);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float zv[4] = {zc[j].x, zc[j].y, zc[j].z, zc[j].w};
+                        float dd[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int col = c0 + 4 * j + e;
+                            // dt_{l-1}/dh_{l-1}: a (affine tail) or tb a + ta b (Eq. 3)
+                            const float tvec = P.mult ? fmaf(tbv, __ldg(P.tw + col), tav * __ldg(P.tw + N + col))
+                                                      : __ldg(P.tw + col);
+                            const float g = fmaf(__uint_as_float(v[4 * j + e]), inv_s, gl * tvec);
+                            dd[e] = g * tr_slope(P.act, zv[e], P.omega0);
+                        }
+                        dst[j] = make_float4(dd[0], dd[1], dd[2], dd[3]);
+                    }
                 }
             }
-            fence_async_smem();  // generic-proxy writes -> visible to the tensor core's async proxy
-            mbar_arrive(smem_u32(&full[s]));
-        }
-        // ------------------------------------------------ epilogue (warps 4..7: TMEM lane quadrant warp & 3)
-        if (warp >= 4 && n_kb > 0) {
-            const int q = warp & 3;
-            const int r = q * 32 + lane;
-            const uint32_t t_lane = tmem + ((uint32_t)(q * 32) << 16);
-            ok = tr_wait_warp(smem_u32(dfull), 0, abort, P.status) && ok;
-            if (ok) {
-                tc_fence_after();
-                const int row = m0 + r;
-                const float inv_s = EPI == TR_DW ? 1.f : __ldg(P.inv_s);
-                float sa = 0.f, sb = 0.f;
-                float gl = 0.f, tav = 0.f, tbv = 0.f;
-                if (EPI == TR_BWD && row < P.M) {
-                    gl = __ldg(P.g_prev + row);
-                    tav = __ldg(P.ta_prev + row);
-                    tbv = __ldg(P.tb_prev + row);
-                }
-                for (int c0 = 0; c0 < N; c0 += 32) {
-                    uint32_t v[32];
-                    tmem_ld32(t_lane + (uint32_t)c0, v);
-                    tmem_wait_ld();
-                    if (row >= P.M) continue;
-                    if (EPI == TR_DW) {
-                        float4 *dst = reinterpret_cast<float4 *>(P.out + ((size_t)blockIdx.y * P.M + row) * N + c0);
-#pragma unroll
-                        for (int j = 0; j < 8; ++j)
-                            dst[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
-                                                 __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
-                    } else if (EPI == TR_FWD) {
-                        float4 *dst = reinterpret_cast<float4 *>(P.out + (size_t)row * N + c0);
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            float z[4];
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const int col = c0 + 4 * j + e;
-                                z[e] = fmaf(__uint_as_float(v[4 * j + e]), inv_s, __ldg(P.bias + col));
-                                const float h = tr_act(P.act, z[e], P.omega0);
-                                sa = fmaf(__ldg(P.tw + col), h, sa);
-                                if (P.mult) sb = fmaf(__ldg(P.tw + N + col), h, sb);
-                            }
-                            dst[j] = make_float4(z[0], z[1], z[2], z[3]);
-                        }
-                    } else {  // TR_BWD
-                        const float4 *zp = reinterpret_cast<const float4 *>(P.z_prev + (size_t)row * N + c0);
-                        float4 *dst = reinterpret_cast<float4 *>(P.out + (size_t)row * N + c0);
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const float4 zz = __ldg(zp + j);
-                            const float zv[4] = {zz.x, zz.y, zz.z, zz.w};
-                            float d[4];
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const int col = c0 + 4 * j + e;
-                                // dt_{l-1}/dh_{l-1}: a (affine tail) or tb a + ta b (Eq. 3)
-                                const float tvec = P.mult ? fmaf(tbv, __ldg(P.tw + col), tav * __ldg(P.tw + N + col))
-                                                          : __ldg(P.tw + col);
-                                const float g = fmaf(__uint_as_float(v[4 * j + e]), inv_s, gl * tvec);
-                                d[e] = g * tr_slope(P.act, zv[e], P.omega0);
-                            }
-                            dst[j] = make_float4(d[0], d[1], d[2], d[3]);
-                        }
-                    }
-                }
-                if (EPI == TR_FWD && row < P.M) {
-                    const float ta = sa + __ldg(P.tbias);
-                    const float tb = P.mult ? sb + __ldg(P.tbias + 1) : 1.f;
-                    P.y_out[row] = __ldg(P.y_prev + row) + ta * tb;
-                    P.ta_out[row] = ta;
-                    P.tb_out[row] = tb;
-                }
+            // the accumulator has been read: the MMAs of the tile after next may overwrite it
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&acc_empty[b]));
+            if (EPI == TR_FWD && live) {
+                const float ta = sa + __ldg(P.tbias);
+                const float tb = P.mult ? sb + __ldg(P.tbias + 1) : 1.f;
+                P.y_out[row] = __ldg(P.y_prev + row) + ta * tb;
+                P.ta_out[row] = ta;
+                P.tb_out[row] = tb;
             }
         }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 1) {
+    if (warp == kTrMmaWarp) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
     }
 }
@@ -389,9 +475,12 @@ __global__ void __launch_bounds__(kTrThreads, 1) tr_gemm_kernel(const TrGemm P) 
 // Per-layer weight scales: s_l = 2^-e with max|W_l| = f 2^e, f in [0.5, 1) (1 for an all-zero layer).
 __global__ void tr_amax_kernel(const float *Wh, int W, float *scale, float *inv_scale) {
     const int li = blockIdx.x;
-    const float *w = Wh + (size_t)li * W * W;
+    const float4 *w = reinterpret_cast<const float4 *>(Wh + (size_t)li * W * W);  // W * W is a multiple of 4
     float m = 0.f;
-    for (int i = threadIdx.x; i < W * W; i += blockDim.x) m = fmaxf(m, fabsf(w[i]));
+    for (int i = threadIdx.x; i < W * W / 4; i += blockDim.x) {
+        const float4 v = w[i];
+        m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
     __shared__ float red[32];
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
@@ -495,49 +584,60 @@ __global__ void tr_top_kernel(const float *ZL, const float *GL, const float *TAL
 
 // Column sums over the rows [s R, (s+1) R) of one layer (blockIdx.y = layer l - 1, blockIdx.x = s),
 // one thread per unit j: sum delta'_l, sum G'_l tb h_l, sum G'_l ta h_l, and for l = 1
-// sum delta'_1 x_c; thread 0 also sum G'_l tb and sum G'_l ta.  Partials [L][S][slots].
+// sum delta'_1 x_c; thread 0 also writes sum G'_l tb and sum G'_l ta.  Partials [L][S][slots].
+// Four rows per iteration with their own accumulators keep four rows of loads in flight.
 constexpr int kTrSlots = 6;  // per unit: db, da, dbt, dW1 x, y, z
 __global__ void tr_colsum_kernel(const float *Z, const float *D, const float *G, const float *TA, const float *TB,
                                  const float *pts, int64_t n, int64_t B, int64_t ld, int W, int act, float w0,
                                  const int *mult_of, int64_t rows_per, float *part, float *part_bias) {
     const int l = blockIdx.y;  // 0-based layer
     const int s = blockIdx.x;
-    const int j = threadIdx.x;
+    const int j = threadIdx.x < W ? threadIdx.x : W - 1;  // threads beyond W repeat the last unit, write nothing
     const int64_t r0 = (int64_t)s * rows_per, r1 = min(B, r0 + rows_per);
     const bool mult = mult_of[l] != 0;
     const float *Zl = Z + (size_t)l * ld * W, *Dl = D + (size_t)l * ld * W;
     const float *Gl = G + (size_t)l * ld, *TAl = TA + (size_t)l * ld, *TBl = TB + (size_t)l * ld;
-    if (j < W) {
-        float sd = 0.f, sa = 0.f, sb = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
-        for (int64_t row = r0; row < r1; ++row) {
-            const float d = Dl[row * W + j];
-            const float g = Gl[row];
-            const float h = tr_act(act, Zl[row * W + j], w0);
-            sd += d;
-            sa = fmaf(g * TBl[row], h, sa);
-            if (mult) sb = fmaf(g * TAl[row], h, sb);
-            if (l == 0 && row < n) {
-                sx = fmaf(d, pts[3 * row], sx);
-                sy = fmaf(d, pts[3 * row + 1], sy);
-                sz = fmaf(d, pts[3 * row + 2], sz);
-            }
+    float a[4][8];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[u][k] = 0.f;
+    // delta' is 0 on padding rows (row >= n), so their coordinates may be any finite value: the
+    // point index is clamped and no load is conditional, which keeps four rows of loads in flight
+    auto add_row = [&](float *acc, int64_t rr) {
+        const float d = Dl[rr * W + j];
+        const float g = Gl[rr];
+        const float tb = TBl[rr], ta = TAl[rr];
+        const float h = tr_act(act, Zl[rr * W + j], w0);
+        acc[0] += d;
+        acc[1] = fmaf(g * tb, h, acc[1]);
+        if (mult) acc[2] = fmaf(g * ta, h, acc[2]);
+        if (l == 0) {
+            const int64_t pr = rr < n ? rr : n - 1;
+            acc[3] = fmaf(d, pts[3 * pr], acc[3]);
+            acc[4] = fmaf(d, pts[3 * pr + 1], acc[4]);
+            acc[5] = fmaf(d, pts[3 * pr + 2], acc[5]);
         }
-        float *p = part + (((size_t)l * gridDim.x + s) * kTrSlots) * W;
-        p[0 * W + j] = sd;
-        p[1 * W + j] = sa;
-        p[2 * W + j] = sb;
-        p[3 * W + j] = sx;
-        p[4 * W + j] = sy;
-        p[5 * W + j] = sz;
+        acc[6] = fmaf(g, tb, acc[6]);
+        acc[7] = fmaf(g, ta, acc[7]);
+    };
+    int64_t row = r0;
+    for (; row + 4 <= r1; row += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) add_row(a[u], row + u);
     }
-    if (j == 0) {
-        float sc = 0.f, se = 0.f;
-        for (int64_t row = r0; row < r1; ++row) {
-            sc = fmaf(Gl[row], TBl[row], sc);
-            se = fmaf(Gl[row], TAl[row], se);
-        }
-        part_bias[((size_t)l * gridDim.x + s) * 2] = sc;
-        part_bias[((size_t)l * gridDim.x + s) * 2 + 1] = mult ? se : 0.f;
+    for (; row < r1; ++row) add_row(a[0], row);
+    float t[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t[k] = (a[0][k] + a[1][k]) + (a[2][k] + a[3][k]);
+    if (threadIdx.x < W) {
+        float *p = part + (((size_t)l * gridDim.x + s) * kTrSlots) * W;
+#pragma unroll
+        for (int k = 0; k < kTrSlots; ++k) p[k * W + j] = t[k];
+    }
+    if (threadIdx.x == 0) {
+        part_bias[((size_t)l * gridDim.x + s) * 2] = t[6];
+        part_bias[((size_t)l * gridDim.x + s) * 2 + 1] = mult ? t[7] : 0.f;
     }
 }
 
@@ -549,21 +649,39 @@ __global__ void tr_finalize_kernel(const float *part, const float *part_bias, co
     const size_t otw = obh + (size_t)(L - 1) * W, otb = otw + (size_t)L * 2 * W;
     const size_t total = otb + (size_t)L * 2;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        float v = 0.f;
+        // the partials of element i: count values `stride` apart from `base` (eight running sums,
+        // added in a fixed order)
+        const float *base;
+        size_t stride;
+        int count;
         if (i >= oWh && i < obh) {  // dW_l, l >= 2: rows out, columns in
             const size_t li = (i - oWh) / ((size_t)W * W), rem = (i - oWh) % ((size_t)W * W);
-            for (int s = 0; s < S_dw; ++s) v += dw_part[((li * S_dw + s) * W) * (size_t)W + rem];
+            base = dw_part + li * S_dw * (size_t)W * W + rem;
+            stride = (size_t)W * W;
+            count = S_dw;
         } else if (i >= otb) {  // tail biases
             const size_t l = (i - otb) / 2, which = (i - otb) % 2;
-            for (int s = 0; s < S; ++s) v += part_bias[(l * S + s) * 2 + which];
+            base = part_bias + l * S * 2 + which;
+            stride = 2;
+            count = S;
         } else {
             int l, slot, j;
             if (i < ob1) { l = 0; slot = 3 + (int)((i - oW1) % 3); j = (int)((i - oW1) / 3); }
             else if (i < oWh) { l = 0; slot = 0; j = (int)(i - ob1); }
             else if (i < otw) { l = 1 + (int)((i - obh) / W); slot = 0; j = (int)((i - obh) % W); }
             else { l = (int)((i - otw) / (2 * W)); slot = 1 + (int)(((i - otw) % (2 * W)) / W); j = (int)((i - otw) % W); }
-            for (int s = 0; s < S; ++s) v += part[(((size_t)l * S + s) * kTrSlots + slot) * W + j];
+            base = part + ((size_t)l * S * kTrSlots + slot) * W + j;
+            stride = (size_t)kTrSlots * W;
+            count = S;
         }
+        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        int s = 0;
+        for (; s + 8 <= count; s += 8) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] += base[(size_t)(s + u) * stride];
+        }
+        for (; s < count; ++s) acc[0] += base[(size_t)s * stride];
+        const float v = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
         grad[i] = v * inv_n;
     }
 }
@@ -615,23 +733,25 @@ struct sand_trainer_s {
 
 namespace {
 
-constexpr int kTrColsumSplits = 64;
+constexpr int kTrColsumSplits = 256;
 constexpr int kTrLossBlocks = 304;
 
 size_t tr_stage_bytes(int N) { return (size_t)2 * kTrBM * 128 + (size_t)2 * N * 128; }
 
 int tr_stages(int N) {
-    const size_t misc = 1024 + 8 * (2 * kTrMaxStages + 2) + 16;
+    const size_t misc = 1024 + 8 * (2 * kTrMaxStages + 5) + 16;
     int s = (int)((kTrSmem - misc) / tr_stage_bytes(N));
     return s > kTrMaxStages ? kTrMaxStages : s;
 }
 
-size_t tr_smem(int N, int stages) { return 1024 + (size_t)stages * tr_stage_bytes(N) + 8 * (2 * kTrMaxStages + 2) + 16; }
+size_t tr_smem(int N, int stages) { return 1024 + (size_t)stages * tr_stage_bytes(N) + 8 * (2 * kTrMaxStages + 5) + 16; }
 
 template <int EPI>
-cudaError_t tr_launch(TrGemm P, dim3 grid, cudaStream_t s) {
+cudaError_t tr_launch(TrGemm P, int num_sms, cudaStream_t s) {
     P.n_stages = tr_stages(P.N);
     P.stage_bytes = (uint32_t)tr_stage_bytes(P.N);
+    const int n_tiles = P.m_tiles * P.splits;
+    const dim3 grid((unsigned)(n_tiles < num_sms ? n_tiles : num_sms));
     const size_t smem = tr_smem(P.N, P.n_stages);
     cudaError_t e = cudaFuncSetAttribute(tr_gemm_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -769,7 +889,7 @@ sand_status sand_train_step(sand_trainer T, const float *d_points, const float *
     auto Dl = [&](int l) { return T->D + (size_t)(l - 1) * cap * W; };
     auto row = [&](float *base, int l) { return base + (size_t)(l - 1) * cap; };
     // weights of this step: scales and split packing
-    tr_amax_kernel<<<L - 1, 256, 0, s>>>(P + oWh, W, T->scale, T->inv_scale);
+    tr_amax_kernel<<<L - 1, 1024, 0, s>>>(P + oWh, W, T->scale, T->inv_scale);
     tr_pack_kernel<<<2 * T->num_sms, 256, 0, s>>>(P + oWh, W, L - 1, T->scale, T->wf, T->wb);
     // forward
     {
@@ -779,7 +899,7 @@ sand_status sand_train_step(sand_trainer T, const float *d_points, const float *
                                                          P + otb, Zl(1), row(T->Y, 1), row(T->TA, 1), row(T->TB, 1));
         SAND_CUDA(cudaGetLastError(), "layer-1 kernel");
     }
-    const dim3 rows_grid((unsigned)(B / kTrBM));
+    const int row_tiles = (int)(B / kTrBM);
     const bool mult = T->tail == SAND_TAIL_MULT;
     for (int l = 2; l <= L; ++l) {
         TrGemm g{};
@@ -803,7 +923,10 @@ sand_status sand_train_step(sand_trainer T, const float *d_points, const float *
         g.ta_out = row(T->TA, l);
         g.tb_out = row(T->TB, l);
         g.status = T->status;
-        SAND_CUDA(tr_launch<TR_FWD>(g, rows_grid, s), "forward GEMM");
+        g.m_tiles = row_tiles;
+        g.splits = 1;
+        g.kb_per_split = W / 64;
+        SAND_CUDA(tr_launch<TR_FWD>(g, T->num_sms, s), "forward GEMM");
     }
     // loss, dL/dt (as the integers G'), delta'_L
     tr_loss_kernel<<<T->loss_blocks, 256, 0, s>>>(T->Y, d_targets, n, B, cap, L, T->G, T->loss_part);
@@ -841,7 +964,10 @@ sand_status sand_train_step(sand_trainer T, const float *d_points, const float *
         g.ta_prev = row(T->TA, l - 1);
         g.tb_prev = row(T->TB, l - 1);
         g.status = T->status;
-        SAND_CUDA(tr_launch<TR_BWD>(g, rows_grid, s), "backward GEMM");
+        g.m_tiles = row_tiles;
+        g.splits = 1;
+        g.kb_per_split = W / 64;
+        SAND_CUDA(tr_launch<TR_BWD>(g, T->num_sms, s), "backward GEMM");
         TrGemm w{};
         w.M = W;
         w.N = W;
@@ -855,7 +981,9 @@ sand_status sand_train_step(sand_trainer T, const float *d_points, const float *
         w.b_ld = W;
         w.out = T->dw_part + (size_t)(l - 2) * T->S_dw * W * W;
         w.status = T->status;
-        SAND_CUDA(tr_launch<TR_DW>(w, dim3((unsigned)m_tiles, (unsigned)splits), s), "weight-gradient GEMM");
+        w.m_tiles = m_tiles;
+        w.splits = splits;
+        SAND_CUDA(tr_launch<TR_DW>(w, T->num_sms, s), "weight-gradient GEMM");
         if (splits < T->S_dw)  // unused split slots must read as zero
             SAND_CUDA(cudaMemsetAsync(w.out + (size_t)splits * W * W, 0, (size_t)(T->S_dw - splits) * W * W * 4, s),
                       "partials reset");

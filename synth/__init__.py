@@ -485,6 +485,47 @@ def pinhole_rays(width: int, height: int, fov_y_deg: float = 45.0, radius: float
 # --------------------------------------------------------------------------
 # Named workloads
 # --------------------------------------------------------------------------
+def scene_surface_points(n: int, seed: int) -> np.ndarray:
+    """n points on the zero level set of scene_sdf: points drawn uniformly on each primitive's
+    surface (sphere: normalised Gaussian directions; torus: uniform angles, accepted with the
+    area weight (R + r cos v) / (R + r)), kept where no other primitive contains them, float64."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    spheres = [((-0.35, 0.0, 0.0), 0.30), ((0.35, 0.10, 0.0), 0.25), ((0.0, -0.30, 0.30), 0.20)]
+    tc, R, r = np.array((0.0, 0.35, -0.20)), 0.35, 0.08
+    out = []
+    have = 0
+    while have < n:
+        k = max(4 * (n - have), 1024)
+        parts = []
+        for c, rad in spheres:
+            v = g.standard_normal((k, 3))
+            parts.append(np.asarray(c) + rad * v / np.linalg.norm(v, axis=1, keepdims=True))
+        u, w = g.uniform(0, 2 * np.pi, k), g.uniform(0, 2 * np.pi, k)
+        keep = g.uniform(0, 1, k) < (R + r * np.cos(w)) / (R + r)
+        ring = R + r * np.cos(w)
+        tor = np.stack([ring * np.cos(u), r * np.sin(w), ring * np.sin(u)], axis=1) + tc
+        parts.append(tor[keep])
+        p = np.concatenate(parts)
+        p = p[np.abs(scene_sdf(p)) < 1e-9]
+        p = p[g.permutation(len(p))]
+        out.append(p)
+        have += len(p)
+    return np.concatenate(out)[:n]
+
+
+def training_batch(n: int, seed: int, surface_frac: float = 0.6, sigma: float = 0.01):
+    """A training batch as Sec. 4.1 samples it, on the analytic scene: surface_frac of the points
+    on the surface, the rest surface points moved by Gaussian noise (sigma), all in [-1, 1]^3, and
+    their exact SDF values as targets.  Returns (points float32 [n, 3], targets float32 [n])."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    k = int(round(surface_frac * n))
+    surf = scene_surface_points(n, seed + 1)
+    jit = surf[k:] + sigma * g.standard_normal((n - k, 3))
+    pts = np.clip(np.concatenate([surf[:k], jit]), -1.0, 1.0).astype(np.float32)
+    pts = pts[g.permutation(n)]
+    return pts, scene_sdf(pts.astype(np.float64)).astype(np.float32)
+
+
 def serve_specs():
     """The three resident models of the serving workload, each with its own level-7 octree of
     the analytic scene (rotated and scaled per model): 8 x 256 SIREN (seed 1), 8 x 336 SIREN
