@@ -340,7 +340,7 @@ def serve_bench(sand, models, precision, pool, run_s: float, sweep_s: float, mem
     runs of run_s seconds at 0.5x and 0.8x of saturation report p50 / p99 request latency
     (submit to result) and aggregate queries/s."""
     import torch
-    precs = {"bf16": ["bf16", "bf16", "bf16"], "fp32": ["fp32", "fp32_simt", "fp32"]}[precision]
+    precs = {"bf16": ["bf16", "bf16", "bf16"], "fp32": ["fp32", "fp32", "fp32"]}[precision]
     out = {"precision_per_model": precs, "n_streams": 4, "mem_budget": mem_budget}
 
     def server():
@@ -381,6 +381,8 @@ def serve_bench(sand, models, precision, pool, run_s: float, sweep_s: float, mem
         out["load_%.1f" % frac] = {k: st[k] for k in ("offered_requests_per_s", "submitted", "dropped", "requests",
                                                       "batches", "p50_ms", "p99_ms", "max_ms", "queries_per_s",
                                                       "max_outstanding", "seconds")}
+        # batches in flight at once on the device: sum of per-batch device spans / wall span
+        out["load_%.1f" % frac]["device_concurrency"] = st["batch_ms_sum"] / st["span_ms"] if st["span_ms"] else None
     return out
 
 
@@ -427,6 +429,43 @@ def train_bench(sand, local: int, steps: int, n: int = 100000):
     tr.close()
     m.free()
     return out
+
+
+def deep_map_bench(sand, local: int, steps: int, level: int = 9):
+    """The benchmark lattice query (8 x 256 SIREN, float32 mode) against the analytic scene's octree
+    refined to `level` (the paper's octrees go to depth 9-10, Table 5), which the library keeps
+    in its brick encoding: SAND queries/s and the bandwidth of the memory-bound stages (lookup,
+    scan, scatter: 42 B per network point) against the HBM copy rate."""
+    import torch
+    model = synth.siren_tmlp(N_LAYERS, WIDTH, seed=SEED)
+    tree = synth.scene_octree(level, N_LAYERS)
+    pts = synth.lattice(GRID)
+    n = len(pts)
+    m = sand.Model.from_params(*model.header_ints(), model.omega0, model.flat(), device=local)
+    m.set_depth_map(tree.max_level, tree.n_layers, tree.child, tree.depth, tree.far)
+    x = torch.from_numpy(pts).cuda()
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    ws = m.workspace(n)
+    for _ in range(3):
+        m.query(x, precision="fp32", out=out, workspace=ws)
+    torch.cuda.synchronize()
+    counts = np.array(m.stats(ws)["count"][:N_LAYERS + 1], np.int64)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    stream = torch.cuda.current_stream()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(steps):
+        m.query(x, precision="fp32", out=out, workspace=ws, events=ev[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    step_ms = t0.elapsed_time(t1) / steps
+    pre_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / steps
+    pk, _ = peaks()
+    m.free()
+    return {"octree_level": level, "octree_nodes": int(tree.n_nodes), "encoding": "bricks of 8^3 finest cells",
+            "queries_per_s": n / (step_ms / 1e3), "ms_per_step": step_ms,
+            "exit_layer_histogram": {str(d): int(c) for d, c in enumerate(counts)},
+            "hbm_stages": hbm_stages(n, int(counts[0]), pre_ms, pk.get("hbm_gbs", 6800.0))}
 
 
 def paper_variants(sand, local: int, steps: int, prec: str, peak_tflops: float, hbm_gbs: float):
@@ -492,10 +531,11 @@ def paper_variants(sand, local: int, steps: int, prec: str, peak_tflops: float, 
     return res
 
 
-def precision_variant(sand, local: int, steps: int, grid: int = 512, n_err: int = 1 << 20):
-    """8 x 256 and 8 x 336 SAND-SIRENs on a grid^3 lattice with bf16 and FP8 hidden products:
-    SAND and full-depth queries/s, tensor-core TFLOP/s, and the error against the FP64 oracle
-    on n_err uniform points in [-1, 1]^3 (PCG64 seed 7; full depth on the first 20,000)."""
+def precision_variant(sand, local: int, steps: int, grid: int = 512, n_err: int = 1 << 20, sine_rate: float = 0.0):
+    """8 x 256 and 8 x 336 SAND-SIRENs on a grid^3 lattice with bf16 and FP8 hidden products (and
+    the 8 x 336 one in the float32 split too): SAND and full-depth queries/s, tensor-core TFLOP/s,
+    the sine pipe's share, and the error against the FP64 oracle on n_err uniform points in
+    [-1, 1]^3 (PCG64 seed 7; full depth on the first 20,000)."""
     import torch
     import oracle
     pts = synth.lattice(grid)
@@ -516,7 +556,7 @@ def precision_variant(sand, local: int, steps: int, grid: int = 512, n_err: int 
         y_ref = oracle.query(model, tree, upts)
         yf_ref = oracle.full_depth(model, upts[:20000])
         entry = {}
-        for prec in ("bf16", "fp8"):
+        for prec in (("fp32", "bf16", "fp8") if width == 336 else ("bf16", "fp8")):
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             for _ in range(2):
                 m.query(x, precision=prec, out=out, workspace=ws)
@@ -544,7 +584,11 @@ def precision_variant(sand, local: int, steps: int, grid: int = 512, n_err: int 
             uy = m.query(ux, precision=prec).double().cpu().numpy()
             e = np.abs(uy - y_ref)
             ufy = m.query(ux[:20000], precision=prec, full_depth=True).double().cpu().numpy()
+            # the co-bound of these modes: one hardware sine per unit and row-layer (Eq. 2)
+            sines = float((np.arange(9) * width * counts).sum())
+            sine_frac = sines / (mlp_ms / 1e3) / sine_rate if sine_rate else None
             entry[prec] = {"sand_queries_per_s": n / (sand_ms / 1e3), "full_depth_queries_per_s": n / (full_ms / 1e3),
+                           "sine_pipe_frac_sand": sine_frac,
                            "sand_ms": sand_ms, "full_ms": full_ms,
                            "tmlp_tflops_sand": flops / (mlp_ms / 1e3) / 1e12,
                            "tflops_full_depth": full_flops / (full_ms / 1e3) / 1e12,
@@ -590,24 +634,59 @@ def trace_bench(sand, model, tree, local: int, steps: int, precision: str = "fp3
     return res
 
 
-def map_build_bench(sand, model, local: int, steps: int):
+def map_build_bench(sand, model, local: int, steps: int, label: str, rs=(1.5e-4, 1e-2)):
     """The network-depth map from the network (Eq. 5-7) for the level-7 scene octree: Eq. 5 on a
-    4^3 lattice per near leaf with r = 1.5e-4, max-pooled per leaf, float32 mode."""
+    4^3 lattice per near leaf, max-pooled per leaf, float32 mode, at the paper's r = 1.5e-4 and a
+    looser r for a briefly trained network."""
     import torch
     tree = synth.scene_octree(7, N_LAYERS, far_field=True)
     near = ((tree.child < 0) & (tree.depth > 0)).astype(np.uint8)
     m = sand.Model.from_params(*model.header_ints(), model.omega0, model.flat(), device=local)
-    got = m.build_depth_map(tree.max_level, tree.child, near, samples_per_axis=4, r=1.5e-4)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        got = m.build_depth_map(tree.max_level, tree.child, near, samples_per_axis=4, r=1.5e-4)
-    dt = (time.perf_counter() - t0) / steps
     n_near = int(near.sum())
+    res = {"model": label, "octree": "scene, level 7, far field", "near_leaves": n_near, "samples_per_leaf": 64,
+           "samples": n_near * 64}
+    for r in rs:
+        got = m.build_depth_map(tree.max_level, tree.child, near, samples_per_axis=4, r=r)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            got = m.build_depth_map(tree.max_level, tree.child, near, samples_per_axis=4, r=r)
+        dt = (time.perf_counter() - t0) / steps
+        res["r=%g" % r] = {"ms": dt * 1e3, "samples_per_s": n_near * 64 / dt,
+                           "depth_histogram": np.bincount(got[near.astype(bool)], minlength=N_LAYERS + 1).tolist()}
     m.free()
-    return {"octree": "scene, level 7, far field", "near_leaves": n_near, "samples_per_leaf": 64,
-            "samples": n_near * 64, "r": 1.5e-4, "ms": dt * 1e3, "samples_per_s": n_near * 64 / dt,
-            "depth_histogram": np.bincount(got[near.astype(bool)], minlength=N_LAYERS + 1).tolist()}
+    return res
+
+
+def trained_scene_model(sand, local: int, steps: int):
+    """The benchmark's 8 x 256 SIREN after `steps` training steps (sand_train_step, Adam at the
+    paper's learning rate 1e-4) on a 100,000-point batch of the analytic scene (60 % surface,
+    40 % jittered), so that Eq. 5 and the dynamic exit see tails that approach the SDF."""
+    import dataclasses
+    import torch
+    from paper_2604_25936_gb300.binding import Trainer
+    model = synth.siren_tmlp(N_LAYERS, WIDTH, seed=SEED)
+    pts, gt = synth.training_batch(100000, seed=22)
+    m = sand.Model.from_params(*model.header_ints(), model.omega0, model.flat(), device=local)
+    tr = Trainer(m, max_points=len(pts))
+    x, t = torch.from_numpy(pts).cuda(), torch.from_numpy(gt).cuda()
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    for _ in range(steps):
+        tr.step(x, t, loss=loss)
+    torch.cuda.synchronize()
+    tr.status()
+    flat = tr.params()
+    final = float(loss.item())
+    tr.close()
+    m.free()
+    parts, o = {}, 0
+    L, W = N_LAYERS, WIDTH
+    for name, shape in (("W1", (W, 3)), ("b1", (W,)), ("Wh", (L - 1, W, W)), ("bh", (L - 1, W)),
+                        ("tail_w", (L, 2, W)), ("tail_b", (L, 2))):
+        k = int(np.prod(shape))
+        parts[name] = flat[o:o + k].reshape(shape).astype(np.float32)
+        o += k
+    return dataclasses.replace(model, **parts), final
 
 
 def dynamic_bench(sand, model, x, n: int, local: int, steps: int):
@@ -979,11 +1058,19 @@ def main():
 
     mapb = None
     if rank == 0 and not args.no_variants:
-        mapb = map_build_bench(sand, model, local, max(2, K // 8))
+        trained, trained_loss = trained_scene_model(sand, local, 1000)
+        mapb = {"random_init": map_build_bench(sand, model, local, max(2, K // 8), "random SIREN init"),
+                "trained": map_build_bench(sand, trained, local, max(2, K // 8),
+                                           "1000 training steps (loss %.4g)" % trained_loss)}
+        dynb = {"random_init": dynb, "trained": dynamic_bench(sand, trained, x, n, local, max(2, K // 8))}
 
     variant = None
     if rank == 0 and not args.no_variants:
-        variant = precision_variant(sand, local, max(3, K // 4))
+        variant = precision_variant(sand, local, max(3, K // 4), sine_rate=sr)
+
+    deepb = None
+    if rank == 0 and not args.no_variants:
+        deepb = deep_map_bench(sand, local, max(3, K // 4))
 
     trainb = None
     if rank == 0 and not args.no_variants:
@@ -1032,6 +1119,7 @@ def main():
         "precision_variant": variant,
         "paper_variants": paperv,
         "training": trainb,
+        "deep_map": deepb,
         "sphere_trace": tr,
         "depth_map_build": mapb,
         "dynamic_exit": dynb,

@@ -121,6 +121,13 @@ typedef struct {
     size_t workspace_bytes;
     void *const *stage_events; /* optional: 3 caller-created cudaEvent_t handles, recorded on the stream
                                before the lookup, before the T-MLP kernel and after it (stage timing) */
+    uint32_t wait_limit_us; /* limit of every bounded wait inside the tensor-core kernel, in microseconds
+                               (0 = 2 s).  A wait that runs out makes the kernel stop issuing work, finish
+                               what is in flight, free its tensor memory and return; the query's results
+                               are then undefined and sand_read_stats reports SAND_ETIMEOUT.  Only the
+                               plain, gradient and all-tails queries take it (dynamic exit and sphere
+                               tracing: SAND_EINVAL) */
+    int32_t reserved;
 } sand_query_opts;
 
 /* Load a model file: "TMLP", u32 version 1, 7 x i32 (n_layers, width, in_dim,
@@ -144,8 +151,12 @@ sand_status sand_load_tmlp_mem(const sand_tmlp_desc *desc, const float *h_params
 sand_status sand_load_depth_map(sand_model m, const char *path);
 
 /* Load the depth map from host arrays (see sand_depth_map_desc).  The octree is
- * re-encoded losslessly on the device as a dense exit-layer grid at max_level
- * plus a dense far-value grid when the map has far leaves. */
+ * re-encoded losslessly on the device at its finest level: up to level 7 as a
+ * dense exit-layer grid (2 MiB at level 7) plus a dense far-value grid when the
+ * map has far leaves; deeper maps (levels 8 .. 10) as a table over the cells of
+ * level max_level - 3 whose entries either hold a leaf's exit layer and far
+ * value or point to a brick of 8^3 finest cells (exit layers, and far values
+ * only for bricks holding far leaves).  SAND_EUNSUPPORTED above level 10. */
 sand_status sand_load_depth_map_mem(sand_model m, const sand_depth_map_desc *desc, const int32_t *h_child,
                                     const uint8_t *h_depth, const float *h_far);
 
@@ -303,6 +314,12 @@ typedef struct {
     double p50_ms, p99_ms, max_ms;       /* submit-to-result latency of completed requests */
     double queries_per_s;                /* points completed / (last completion - first submit) */
     size_t arena_bytes;
+    double span_ms;                      /* last completion - first submit */
+    double batch_ms_sum;                 /* sum over completed batches of their time on the device, from
+                                            an event before their first copy to one after their last:
+                                            above span_ms when batches were in flight at once (copies
+                                            of one beside the query of another; the tensor-core kernel
+                                            takes every SM, so two queries' kernels queue) */
 } sand_server_report;
 /* Start a server over n_models loaded models (all on one device).  Packs their
  * weights for opts->precision and reserves the arena; nothing is allocated later. */

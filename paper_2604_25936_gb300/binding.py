@@ -46,7 +46,8 @@ class DepthMapDesc(ctypes.Structure):
 class QueryOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_depth", ctypes.c_int32), ("full_depth", ctypes.c_int32),
                 ("all_tails", ctypes.c_int32), ("d_exit_layers", ctypes.c_void_p), ("d_workspace", ctypes.c_void_p),
-                ("workspace_bytes", ctypes.c_size_t), ("stage_events", ctypes.c_void_p)]
+                ("workspace_bytes", ctypes.c_size_t), ("stage_events", ctypes.c_void_p),
+                ("wait_limit_us", ctypes.c_uint32), ("reserved", ctypes.c_int32)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -57,7 +58,8 @@ class ServerOpts(ctypes.Structure):
 class ServerReport(ctypes.Structure):
     _fields_ = [("requests", ctypes.c_int64), ("batches", ctypes.c_int64), ("points", ctypes.c_int64),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
-                ("queries_per_s", ctypes.c_double), ("arena_bytes", ctypes.c_size_t)]
+                ("queries_per_s", ctypes.c_double), ("arena_bytes", ctypes.c_size_t), ("span_ms", ctypes.c_double),
+                ("batch_ms_sum", ctypes.c_double)]
 
 
 class TraceOpts(ctypes.Structure):

@@ -21,6 +21,10 @@ struct sand_model_s {
     sand::TcModel tc{};               // packed tensor-core weights (per precision, built lazily)
     uint8_t *d_grid = nullptr;        // dense exit-layer grid
     float *d_far = nullptr;           // dense far-value grid (only when the map has far leaves)
+    uint2 *d_coarse = nullptr;        // brick encoding of deeper maps: coarse table, bricks, far blocks
+    uint8_t *d_bricks = nullptr;
+    float *d_farblk = nullptr;
+    size_t map_bytes = 0;             // device bytes of the map's encoding
     int map_level = -1;
     void *d_ws = nullptr;             // default workspace
     size_t ws_bytes = 0;
@@ -137,6 +141,9 @@ static void release(sand_model_s *m) {
     tc_release(&m->tc);
     cudaFree(m->d_grid);
     cudaFree(m->d_far);
+    cudaFree(m->d_coarse);
+    cudaFree(m->d_bricks);
+    cudaFree(m->d_farblk);
     cudaFree(m->d_ws);
     cudaFree(m->d_stage);
     cudaFree(m->d_trace);
@@ -197,6 +204,89 @@ static sand_status densify(const sand_depth_map_desc &d, const int32_t *child, c
                 if (has_far)
                     for (int64_t x = it.cx * s; x < (it.cx + 1) * s; ++x) fgrid[row + x] = far[it.node];
             }
+    }
+    return SAND_OK;
+}
+
+// Brick encoding of a map deeper than kDenseMaxLevel (iterative descent; validates the tree like
+// densify): leaves at or above the coarse level (max_level - 3) fill coarse entries directly;
+// a node at the coarse level with children becomes a brick of 8^3 finest cells.
+static sand_status brickify(const sand_depth_map_desc &d, const int32_t *child, const uint8_t *depth, const float *far,
+                            int model_layers, std::vector<uint2> &coarse, std::vector<uint8_t> &bricks,
+                            std::vector<float> &farblk) {
+    const int ML = d.max_level, CL = ML - 3;
+    const int64_t Rc = (int64_t)1 << CL;
+    coarse.assign((size_t)(Rc * Rc * Rc), make_uint2(0x80000000u, 0u));
+    bricks.clear();
+    farblk.clear();
+    struct Item { int32_t node; int level; int64_t cx, cy, cz; };
+    std::vector<Item> stack, sub;
+    stack.push_back({0, 0, 0, 0, 0});
+    int64_t visited = 0;
+    auto check_node = [&](const Item &it, int32_t c) -> sand_status {
+        if (++visited > d.n_nodes) { set_error("octree has a cycle or shared children"); return SAND_EFORMAT; }
+        if (c >= 0) {
+            if (it.level >= ML) { set_error("node %d below max_level %d", it.node, ML); return SAND_EFORMAT; }
+            if ((int64_t)c + 8 > d.n_nodes || c <= it.node) { set_error("bad child index %d at node %d", c, it.node); return SAND_EFORMAT; }
+        } else {
+            const int dv = depth[it.node];
+            if (dv > d.n_layers || dv > model_layers) { set_error("leaf %d exit layer %d exceeds %d layers", it.node, dv, model_layers); return SAND_EFORMAT; }
+        }
+        return SAND_OK;
+    };
+    while (!stack.empty()) {
+        const Item it = stack.back();
+        stack.pop_back();
+        const int32_t c = child[it.node];
+        sand_status st = check_node(it, c);
+        if (st) return st;
+        if (c < 0) {  // a leaf covering (2^(CL - level))^3 coarse cells
+            uint32_t fbits;
+            memcpy(&fbits, &far[it.node], 4);
+            const int64_t s = (int64_t)1 << (CL - it.level);
+            for (int64_t z = it.cz * s; z < (it.cz + 1) * s; ++z)
+                for (int64_t y = it.cy * s; y < (it.cy + 1) * s; ++y)
+                    for (int64_t x = it.cx * s; x < (it.cx + 1) * s; ++x)
+                        coarse[(size_t)((z * Rc + y) * Rc + x)] = make_uint2(0x80000000u | depth[it.node], fbits);
+            continue;
+        }
+        if (it.level < CL) {
+            for (int o = 0; o < 8; ++o)
+                stack.push_back({c + o, it.level + 1, 2 * it.cx + (o & 1), 2 * it.cy + ((o >> 1) & 1), 2 * it.cz + ((o >> 2) & 1)});
+            continue;
+        }
+        // a brick: the subtree below this coarse cell, at the finest level (8 cells per axis)
+        const uint32_t b = (uint32_t)(bricks.size() / 512);
+        bricks.resize(bricks.size() + 512, 0);
+        uint32_t fb = 0xFFFFFFFFu;
+        sub.clear();
+        for (int o = 0; o < 8; ++o) sub.push_back({c + o, it.level + 1, o & 1, (o >> 1) & 1, (o >> 2) & 1});
+        while (!sub.empty()) {
+            const Item s2 = sub.back();
+            sub.pop_back();
+            const int32_t c2 = child[s2.node];
+            st = check_node(s2, c2);
+            if (st) return st;
+            if (c2 >= 0) {
+                for (int o = 0; o < 8; ++o)
+                    sub.push_back({c2 + o, s2.level + 1, 2 * s2.cx + (o & 1), 2 * s2.cy + ((o >> 1) & 1), 2 * s2.cz + ((o >> 2) & 1)});
+                continue;
+            }
+            const int dv = depth[s2.node];
+            if (dv == 0 && fb == 0xFFFFFFFFu) {
+                fb = (uint32_t)(farblk.size() / 512);
+                farblk.resize(farblk.size() + 512, 0.f);
+            }
+            const int64_t s = (int64_t)1 << (ML - s2.level);
+            for (int64_t z = s2.cz * s; z < (s2.cz + 1) * s; ++z)
+                for (int64_t y = s2.cy * s; y < (s2.cy + 1) * s; ++y)
+                    for (int64_t x = s2.cx * s; x < (s2.cx + 1) * s; ++x) {
+                        const size_t local = (size_t)((z * 8 + y) * 8 + x);
+                        bricks[(size_t)b * 512 + local] = (uint8_t)dv;
+                        if (dv == 0) farblk[(size_t)fb * 512 + local] = far[s2.node];
+                    }
+        }
+        coarse[(size_t)((it.cz * Rc + it.cy) * Rc + it.cx)] = make_uint2(b, fb);
     }
     return SAND_OK;
 }
@@ -310,25 +400,45 @@ sand_status sand_load_depth_map_mem(sand_model m, const sand_depth_map_desc *des
     sand_status st = model_precheck(m);
     if (st) return st;
     if (!desc || !h_child || !h_depth || !h_far) { set_error("NULL argument"); return SAND_EINVAL; }
-    if (desc->max_level < 0 || desc->max_level > 9) { set_error("max_level %d outside 0..9", desc->max_level); return SAND_EUNSUPPORTED; }
+    if (desc->max_level < 0 || desc->max_level > kMaxMapLevel) {
+        set_error("max_level %d outside 0..%d", desc->max_level, kMaxMapLevel);
+        return SAND_EUNSUPPORTED;
+    }
     if (desc->n_nodes < 1) { set_error("empty octree"); return SAND_EFORMAT; }
+    const bool dense = desc->max_level <= kDenseMaxLevel;
     std::vector<uint8_t> grid;
     std::vector<float> fgrid;
+    std::vector<uint2> coarse;
     bool has_far = false;
-    st = densify(*desc, h_child, h_depth, h_far, m->desc.n_layers, grid, fgrid, has_far);
+    if (dense) st = densify(*desc, h_child, h_depth, h_far, m->desc.n_layers, grid, fgrid, has_far);
+    else st = brickify(*desc, h_child, h_depth, h_far, m->desc.n_layers, coarse, grid, fgrid);
     if (st) return st;
     DeviceGuard g(m->device);
-    cudaFree(m->d_grid);
-    cudaFree(m->d_far);
+    for (void *p : {(void *)m->d_grid, (void *)m->d_far, (void *)m->d_coarse, (void *)m->d_bricks, (void *)m->d_farblk})
+        cudaFree(p);
     m->d_grid = nullptr;
     m->d_far = nullptr;
+    m->d_coarse = nullptr;
+    m->d_bricks = nullptr;
+    m->d_farblk = nullptr;
     m->map_level = -1;
-    SAND_CUDA(cudaMalloc(&m->d_grid, grid.size()), "cudaMalloc(depth grid)");
-    SAND_CUDA(cudaMemcpy(m->d_grid, grid.data(), grid.size(), cudaMemcpyHostToDevice), "cudaMemcpy(depth grid)");
-    if (has_far) {
-        SAND_CUDA(cudaMalloc(&m->d_far, fgrid.size() * sizeof(float)), "cudaMalloc(far grid)");
-        SAND_CUDA(cudaMemcpy(m->d_far, fgrid.data(), fgrid.size() * sizeof(float), cudaMemcpyHostToDevice), "cudaMemcpy(far grid)");
+    m->map_bytes = 0;
+    auto upload = [&](void **dst, const void *src, size_t bytes, const char *what) -> sand_status {
+        if (!bytes) return SAND_OK;
+        SAND_CUDA(cudaMalloc(dst, bytes), what);
+        SAND_CUDA(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice), what);
+        m->map_bytes += bytes;
+        return SAND_OK;
+    };
+    if (dense) {
+        st = upload((void **)&m->d_grid, grid.data(), grid.size(), "depth grid upload");
+        if (!st && has_far) st = upload((void **)&m->d_far, fgrid.data(), fgrid.size() * sizeof(float), "far grid upload");
+    } else {
+        st = upload((void **)&m->d_coarse, coarse.data(), coarse.size() * sizeof(uint2), "coarse table upload");
+        if (!st) st = upload((void **)&m->d_bricks, grid.data(), grid.size(), "brick upload");
+        if (!st) st = upload((void **)&m->d_farblk, fgrid.data(), fgrid.size() * sizeof(float), "far block upload");
     }
+    if (st) return st;
     m->map_level = desc->max_level;
     return SAND_OK;
 }
@@ -424,7 +534,7 @@ static sand_status run_query(sand_model m, const float *d_points, int64_t n, flo
     if (ev) SAND_CUDA(cudaEventRecord(ev[0], s), "event record");
     SAND_CUDA(launch_init_header(ws, s), "workspace reset");
     if (!o.full_depth) {
-        MapDev map{m->d_grid, m->d_far, m->map_level, m->desc.n_layers};
+        MapDev map{m->d_grid, m->d_far, m->map_level, m->desc.n_layers, m->d_coarse, m->d_bricks, m->d_farblk};
         SAND_CUDA(launch_lookup(map, d_points, n, o.max_depth, d_out, d_grad, o.d_exit_layers, ws, s, d_count),
                   "lookup kernel");
         SAND_CUDA(launch_scatter(d_points, n, m->desc.n_layers, ws, s, d_count), "scatter kernel");
@@ -436,7 +546,7 @@ static sand_status run_query(sand_model m, const float *d_points, int64_t n, flo
         st = tc_prepare(&m->tc, m->desc, m->params.data(), o.precision);
         if (st) return st;
         SAND_CUDA(launch_tmlp_tc(m->tc, m->simt, d_points, n, o.full_depth, ws, d_out, m->num_sms, s, o.all_tails, 0.f,
-                                 nullptr, d_grad),
+                                 nullptr, d_grad, (uint64_t)o.wait_limit_us * 1000ull),
                   "tensor-core T-MLP kernel");
     }
     if (ev) SAND_CUDA(cudaEventRecord(ev[2], s), "event record");
@@ -530,7 +640,8 @@ sand_status sand_query_sdf_dynamic(sand_model m, const float *d_points, int64_t 
     }
     sand_query_opts o{};
     if (opts) o = *opts;
-    if (o.full_depth || o.all_tails || o.d_exit_layers || o.max_depth || o.d_workspace || o.stage_events) {
+    if (o.full_depth || o.all_tails || o.d_exit_layers || o.max_depth || o.d_workspace || o.stage_events ||
+        o.wait_limit_us) {
         set_error("dynamic queries take only the precision from the query options");
         return SAND_EINVAL;
     }

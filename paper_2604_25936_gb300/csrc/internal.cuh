@@ -29,11 +29,23 @@ struct TmlpDev {
     const float *tb;                // [L][2]
 };
 
+// Device encodings of the depth map (lossless re-encodings of the octree at its finest level).
+//   dense (levels <= kDenseMaxLevel): grid[R^3] exit layer per finest cell (x fastest), far[R^3]
+//     the stored SDF per finest cell, or nullptr when the map has no far leaves;
+//   bricks (deeper maps): one entry per cell of level - 3 (R/8 per axis, x fastest).  An entry
+//     {0x80000000 | d, far bits} is a cell inside one leaf of exit layer d; an entry {b, f} points
+//     to brick b: 8^3 exit layers (x fastest) at bricks[512 b ..], and, when any of them is 0,
+//     their stored SDF values at far_blocks[512 f ..] (f = 0xFFFFFFFF: no far leaf in the brick).
+constexpr int kDenseMaxLevel = 7;
+constexpr int kMaxMapLevel = 10;
 struct MapDev {
-    const uint8_t *grid;  // [R^3] exit layer per finest cell, x fastest
-    const float *far;     // [R^3] stored SDF per finest cell, or nullptr when the map has no far leaves
+    const uint8_t *grid;
+    const float *far;
     int level;            // R = 1 << level
     int n_layers;
+    const uint2 *coarse;  // brick encoding (nullptr: dense)
+    const uint8_t *bricks;
+    const float *far_blocks;
 };
 
 // Workspace header, at offset 0 of every query workspace.

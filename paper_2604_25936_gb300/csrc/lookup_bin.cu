@@ -71,11 +71,27 @@ lookup_kernel(MapDev map, const float *__restrict__ pts, int64_t n, int64_t per_
                     if (grad) grad[3 * i] = grad[3 * i + 1] = grad[3 * i + 2] = qnan;
                 } else {
                     const int ix = cell_index(x, hr, half), iy = cell_index(y, hr, half), iz = cell_index(z, hr, half);
-                    const int64_t c = ((int64_t)iz * R + iy) * R + ix;
-                    int d = __ldg(map.grid + c);
+                    int d;
+                    float fv = 0.0f;
+                    if (!map.coarse) {  // dense grid
+                        const int64_t c = ((int64_t)iz * R + iy) * R + ix;
+                        d = __ldg(map.grid + c);
+                        if (d == 0 && map.far) fv = __ldg(map.far + c);
+                    } else {  // coarse table of cells 8 finest cells wide, then a brick
+                        const int Rc = R >> 3;
+                        const uint2 e = __ldg(map.coarse + ((int64_t)(iz >> 3) * Rc + (iy >> 3)) * Rc + (ix >> 3));
+                        if (e.x & 0x80000000u) {
+                            d = (int)(e.x & 0xFFu);
+                            fv = __uint_as_float(e.y);
+                        } else {
+                            const int local = (((iz & 7) << 3) + (iy & 7)) * 8 + (ix & 7);
+                            d = __ldg(map.bricks + (size_t)e.x * 512 + local);
+                            if (d == 0 && e.y != 0xFFFFFFFFu) fv = __ldg(map.far_blocks + (size_t)e.y * 512 + local);
+                        }
+                    }
                     if (d > 0 && max_depth > 0 && d > max_depth) d = max_depth;
                     if (d == 0) {
-                        if (out) out[i] = map.far ? __ldg(map.far + c) : 0.0f;
+                        if (out) out[i] = fv;
                         if (grad) grad[3 * i] = grad[3 * i + 1] = grad[3 * i + 2] = 0.0f;
                     }
                     e = (uint8_t)d;

@@ -102,7 +102,7 @@ struct Batch {
     std::vector<Request *> reqs;
     int64_t points = 0;
     size_t off = 0, bytes = 0;
-    cudaEvent_t done = nullptr;
+    cudaEvent_t start = nullptr, done = nullptr;  // around the batch's copies and query on its stream
     bool launched = false;  // set (under the server mutex) once every copy, the query and the event are enqueued
 };
 
@@ -123,6 +123,7 @@ struct sand_server_s {
     std::vector<double> latencies_ms;
     uint64_t next_id = 1;
     int64_t points_done = 0, batches_done = 0, requests_done = 0;
+    double batch_ms_sum = 0.0;  // sum over completed batches of their time on the device (start to done event)
     sand::Clock::time_point t_first, t_last;
     bool any = false, stop = false;
     std::thread scheduler, completer;
@@ -141,6 +142,7 @@ static void launch_batch(sand_server_s *S, int slot, Batch *b) {
     void *ws = base + align_up((size_t)b->points * 12, 256) + align_up((size_t)b->points * 4, 256);
     sand_status st_q = SAND_OK;
     int64_t o = 0;
+    cudaEventRecord(b->start, st);
     for (Request *r : b->reqs) {
         if (cudaMemcpyAsync(d_pts + 3 * o, r->h_points, (size_t)r->n * 12, cudaMemcpyHostToDevice, st) != cudaSuccess)
             st_q = SAND_ECUDA;
@@ -222,7 +224,8 @@ static void scheduler_loop(sand_server_s *S) {
             continue;
         }
         S->in_flight[slot] = b;  // occupies the stream; polled only once launched (an unrecorded event reads as complete)
-        cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+        cudaEventCreate(&b->start);
+        cudaEventCreate(&b->done);
         lk.unlock();
         launch_batch(S, slot, b);
         lk.lock();
@@ -254,7 +257,10 @@ static void completion_loop(sand_server_s *S) {
             S->points_done += b->points;
             S->batches_done++;
             S->t_last = now;
+            float ms = 0.f;
+            if (e == cudaSuccess && cudaEventElapsedTime(&ms, b->start, b->done) == cudaSuccess) S->batch_ms_sum += ms;
             S->arena.free(b->off, b->bytes);
+            cudaEventDestroy(b->start);
             cudaEventDestroy(b->done);
             delete b;
             S->in_flight[i] = nullptr;
@@ -416,6 +422,8 @@ sand_status sand_server_stats(sand_server S, sand_server_report *out) {
     const double span = S->any ? std::chrono::duration<double>(S->t_last - S->t_first).count() : 0.0;
     out->queries_per_s = span > 0 ? S->points_done / span : 0.0;
     out->arena_bytes = S->arena.size();
+    out->span_ms = span * 1e3;
+    out->batch_ms_sum = S->batch_ms_sum;
     return SAND_OK;
 }
 

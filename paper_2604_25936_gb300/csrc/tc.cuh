@@ -19,7 +19,7 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
 // grad: also dy/dx per point ([n][3], forward-mode tangents as three more rows per point).
 cudaError_t launch_tmlp_tc(const TcModel &tc, const TmlpDev &M, const float *pts, int64_t n, int full_depth, void *ws,
                            float *out, int num_sms, cudaStream_t s, int all_tails = 0, float dyn_r = 0.f,
-                           uint8_t *exit_out = nullptr, float *grad = nullptr);
+                           uint8_t *exit_out = nullptr, float *grad = nullptr, uint64_t wait_ns = 0);
 void tc_release(TcModel *tc);
 
 }  // namespace sand

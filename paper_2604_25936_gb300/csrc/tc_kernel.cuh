@@ -70,7 +70,12 @@ constexpr int kEpiWarps = 4 * kSlices;
 // other variants keep 320 threads: carried in a full-depth kernel, the extra warps' code costs
 // its epilogue registers.
 constexpr int kCcWarps = 2;
-constexpr int tc_threads(int var) { return 64 + 32 * (kEpiWarps + (var == 3 ? kCcWarps : 0)); }
+constexpr int tc_threads(int var) { return 64 + 32 * (kEpiWarps + ((var & 3) == 3 ? kCcWarps : 0)); }
+// Variant bit 2 (float32 split mode at W = 336 only): the lo part of the activations lives in
+// shared memory instead of TMEM, where the accumulator (336 columns) and the hi part (168) leave
+// no room for it; the MMAs read it through a shared-memory descriptor, and a weight stage holds
+// one part (hi or lo) of one K-block.
+constexpr int kAloVar = 4;
 constexpr int kTileM = 128;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
@@ -116,6 +121,8 @@ struct TcParams {
     const float4 *w1p;        // [W]: s (W1[j][0], W1[j][1], W1[j][2], b1[j]) of a raw-coordinate layer 1,
                               // s = omega0 for the sine families (the phase in radians), 1 for ReLU
     int cc;                   // exit-layer-1 rows of a SAND query run on the CUDA-core warps (raw coordinates)
+    uint64_t wait_ns;         // limit of each bounded pipeline wait (the drains after an abort keep 2 s)
+    int alo;                  // float32 mode at W = 336: A_lo in shared memory (kernel variant bit kAloVar)
 };
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -146,17 +153,19 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: false after 2 s, or (when follow_abort) once another thread of the
-// CTA has aborted.  The epilogue warps do not follow the flag: every waiter on a
-// phase then agrees on whether it completed, so none is left alone at a named barrier.
+// Bounded wait: false after `limit` ns (2 s unless the caller set a limit), or (when
+// follow_abort) once another thread of the CTA has aborted.  The epilogue warps do not follow
+// the flag: every waiter on a phase then agrees on whether it completed, so none is left alone
+// at a named barrier; they make each result warp-uniform (__all_sync) before the next
+// warp-collective TMEM access.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort, WsHeader *hdr,
-                                          uint32_t site, bool follow_abort) {
+                                          uint32_t site, bool follow_abort, uint64_t limit) {
     if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     while (true) {
         if (mbar_try(bar, parity)) return true;
         if (follow_abort && *abort) return false;
-        if (globaltimer() - t0 > kTimeoutNs) {
+        if (globaltimer() - t0 > limit) {
             *abort = 1;
             atomicOr(&hdr->flags, (uint32_t)SAND_FLAG_TIMEOUT);
             atomicExch(&hdr->timeout_where, site);
@@ -394,7 +403,9 @@ __device__ __forceinline__ void tmem_st_half(uint32_t taddr, const uint32_t *v) 
 // pre-activation is the derivative of the value row's, without the bias; its activation is
 // cos(u) du (sine, one hardware sine of u + pi/2 for the point's u) or [u > 0] du (ReLU);
 // FINER: cos(p) (1 + 2 |u| k) du with p = u + u |u| k its phase.
-template <int MODE, int ACT, int TAIL, bool GRAD = false>
+// ALO: a_lo is the shared-memory address of this row in the first 16 KB K-block tile of the A_lo
+// operand (128-byte rows, 128-byte swizzle, tiles 1024-byte aligned), not a TMEM address.
+template <int MODE, int ACT, int TAIL, bool GRAD = false, bool ALO = false>
 __device__ __forceinline__ void epilogue16(const float *cs, int W, float c1, const uint32_t *v, int c0, bool write_a,
                                            uint32_t a_hi, uint32_t a_lo, float &sa, float &sb, bool is_val, float fk) {
     constexpr bool MULT = TAIL == SAND_TAIL_MULT;
@@ -452,7 +463,15 @@ __device__ __forceinline__ void epilogue16(const float *cs, int W, float c1, con
             tmem_st4(a_hi + (uint32_t)(c0 >> 2), p8);
         } else {
             tmem_st8(a_hi + (uint32_t)(c0 >> 1), phi);
-            if (MODE == TC_SPLIT16) tmem_st8(a_lo + (uint32_t)(c0 >> 1), plo);
+            if (MODE == TC_SPLIT16 && !ALO) tmem_st8(a_lo + (uint32_t)(c0 >> 1), plo);
+            if (MODE == TC_SPLIT16 && ALO) {  // units c0 .. c0+15: two 16-byte chunks of K-block c0 / 64
+                const uint32_t row = a_lo + (uint32_t)(c0 >> 6) * 16384u, sw = (a_lo >> 7) & 7u;
+                const uint32_t c = (uint32_t)(c0 & 63) >> 3;
+                asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(row + (((c ^ sw)) << 4)), "r"(plo[0]),
+                             "r"(plo[1]), "r"(plo[2]), "r"(plo[3]) : "memory");
+                asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(row + ((((c + 1) ^ sw)) << 4)), "r"(plo[4]),
+                             "r"(plo[5]), "r"(plo[6]), "r"(plo[7]) : "memory");
+            }
         }
     }
 }
@@ -463,9 +482,10 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                const float4 *__restrict__ sorted, WsHeader *hdr, int64_t n, int full_depth, float *__restrict__ out) {
     constexpr int PARTS = MODE == TC_SPLIT16 ? 2 : 1;
     constexpr bool MULT = TAIL == SAND_TAIL_MULT;
-    constexpr bool EXT = VAR == 1;   // extended outputs: all tails, dynamic exit
-    constexpr bool GRAD = VAR == 2;  // value and input gradient: 32 points x 4 rows per tile
-    constexpr bool CCW = VAR == 3;   // SAND query with the exit-layer-1 rows on the CUDA-core warps
+    constexpr bool EXT = (VAR & 3) == 1;   // extended outputs: all tails, dynamic exit
+    constexpr bool GRAD = (VAR & 3) == 2;  // value and input gradient: 32 points x 4 rows per tile
+    constexpr bool CCW = (VAR & 3) == 3;   // SAND query with the exit-layer-1 rows on the CUDA-core warps
+    constexpr bool ALO = (VAR & kAloVar) != 0 && MODE == TC_SPLIT16;  // A_lo in shared memory
     constexpr int PPT = GRAD ? kTileM / 4 : kTileM;  // points per tile
     constexpr int UPS = MODE == TC_FP8 ? 128 : 64;  // K-units per weight stage (one 128-byte row per unit)
     constexpr int UPK = MODE == TC_FP8 ? 32 : 16;   // K-units per MMA (32 bytes of every row)
@@ -477,7 +497,9 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
     const int W = P.W, L = P.L;
     const int KB = (W + 63) >> 6;   // K-blocks of 64 units (the last one partial when W % 64 != 0)
     const bool drain_first = (W & 63) == 0 && KB <= 4;  // else: serial epilogue (see below)
-    uint8_t *stage_base = smem;
+    const int KBP = (W + 63) >> 6;  // K-blocks of the A_lo operand in shared memory (ALO)
+    uint8_t *alo_base = smem;
+    uint8_t *stage_base = smem + (ALO ? (size_t)KBP * 16384 : 0);
     float *c_all = reinterpret_cast<float *>(stage_base + (size_t)P.n_stages * P.stage_bytes);  // [L][3][W]
     uint64_t *bars = reinterpret_cast<uint64_t *>(c_all + (size_t)3 * L * W);
     uint64_t *full_bar = bars;
@@ -548,18 +570,20 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                 const int Dt = tile_depth(t);
                 for (int l = P.first_mma; l <= Dt && ok; ++l) {
                     const int kb_n = ((l == 1 ? P.D : W) + UPS - 1) / UPS;
-                    const int parts_l = (l == 1 && P.l1_fold) ? 1 : PARTS;  // the folded layer 1 has one block
-                    const int sb_n = (kb_n + KBS - 1) / KBS;
+                    const bool fold_l = l == 1 && P.l1_fold;
+                    const int parts_l = fold_l ? 1 : PARTS;  // the folded layer 1 has one block
+                    // ALO: one part of one K-block per stage (hi of kb, then lo of kb)
+                    const int sb_n = ALO ? (fold_l ? 1 : 2 * kb_n) : (kb_n + KBS - 1) / KBS;
                     for (int sb = 0; sb < sb_n && ok; ++sb, ++it) {
                         const uint32_t s = it % P.n_stages, ph = (it / P.n_stages) & 1;
-                        ok = mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1, abort, hdr, 1, true);
+                        ok = mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1, abort, hdr, 1, true, P.wait_ns);
                         if (!ok) break;
                         // sub-block j: part j of K-block sb (float32 mode), or K-block KBS sb + j
-                        const int subs = PARTS == 2 ? parts_l : min(KBS, kb_n - sb * KBS);
+                        const int subs = ALO ? 1 : PARTS == 2 ? parts_l : min(KBS, kb_n - sb * KBS);
                         mbar_arrive_tx(smem_u32(&full_bar[s]), (uint32_t)subs * (uint32_t)W * 128u);
                         for (int j = 0; j < subs; ++j) {
-                            const int p = PARTS == 2 ? j : 0;
-                            const int kb = PARTS == 2 ? sb : sb * KBS + j;
+                            const int p = ALO ? (fold_l ? 0 : (sb & 1)) : PARTS == 2 ? j : 0;
+                            const int kb = ALO ? (fold_l ? 0 : (sb >> 1)) : PARTS == 2 ? sb : sb * KBS + j;
                             const int row0 = ((l - P.first_mma) * PARTS + p) * W;
                             for (int bx = 0; bx < W; bx += P.box_rows)  // one box of W rows, or two of W/2
                                 tma_load_2d(smem_u32(stage_base + (size_t)s * P.stage_bytes + (size_t)(j * W + bx) * 128),
@@ -609,25 +633,26 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                     const int kb_n = (K + UPS - 1) / UPS;
                     const int ks_n = (K + UPK - 1) / UPK;  // the last FP8 K-step may be half zero padding
                     int e_seen = -1;  // last 64-unit block of the A operand waited for in this layer
-                    ok = mbar_wait(smem_u32(&full_bar[s]), ph, abort, hdr, 3, true);
+                    ok = mbar_wait(smem_u32(&full_bar[s]), ph, abort, hdr, 3, true, P.wait_ns);
                     if (!ok) break;
                     if (any_layer && drained_credit) {
                         drained_credit = false;
                     } else if (any_layer) {  // the previous layer's accumulator has been read out
-                        ok = mbar_wait(smem_u32(d_drained), pdr, abort, hdr, 8, true);
+                        ok = mbar_wait(smem_u32(d_drained), pdr, abort, hdr, 8, true, P.wait_ns);
                         pdr ^= 1;
                         if (!ok) break;
                     }
                     any_layer = true;
                     const bool fold = l == 1 && P.l1_fold;
-                    const int sb_n = (kb_n + KBS - 1) / KBS;
+                    const int sb_n = ALO ? (fold ? 1 : 2 * kb_n) : (kb_n + KBS - 1) / KBS;
                     for (int sb = 0; sb < sb_n && ok; ++sb) {
-                        if (sb > 0) ok = mbar_wait(smem_u32(&full_bar[s]), ph, abort, hdr, 3, true);
+                        if (sb > 0) ok = mbar_wait(smem_u32(&full_bar[s]), ph, abort, hdr, 3, true, P.wait_ns);
                         if (!ok) break;
                         tc_fence_after();
                         const uint64_t bd_stage = bd_base + (uint64_t)s * bd_step;
+                        const int part = ALO && !fold ? (sb & 1) : 0;  // ALO: the stage's weights are hi (0) or lo (1)
                         for (int jb = 0; jb < KBS && ok && !tile_skip; ++jb) {
-                            const int kb = sb * KBS + jb;
+                            const int kb = ALO ? (fold ? 0 : sb >> 1) : sb * KBS + jb;
                             if (kb >= kb_n) break;
                             const uint64_t bd = bd_stage + (uint64_t)(jb * W) * 8u;  // this K-block's sub-block
                             const uint64_t bd_lo = bd_stage + (uint64_t)W * 8u;  // float32 mode: the lo weights
@@ -639,7 +664,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                                 const int g = kb * 4 + g0;
                                 const int e = (g * UPK) >> 6;  // block of the A operand these K-steps read
                                 if (e > e_seen) {
-                                    ok = mbar_wait(smem_u32(&a_ready[e]), pa[e], abort, hdr, 2, true);
+                                    ok = mbar_wait(smem_u32(&a_ready[e]), pa[e], abort, hdr, 2, true, P.wait_ns);
                                     pa[e] ^= 1;
                                     e_seen = e;
                                     if (!ok) break;
@@ -665,7 +690,17 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                                     const uint32_t id = grp ? idesc1 : idesc0;
                                     const uint64_t goff = (uint64_t)(2 * g0) + (grp ? (uint64_t)n0 * 8u : 0u);
                                     const uint64_t bk = bd + goff;
-                                    if (PARTS == 2 && cnt == 4) {
+                                    if (ALO) {  // A_hi B_hi + A_lo B_hi (hi stage) or A_hi B_lo (lo stage)
+                                        const uint32_t alo_k = smem_u32(alo_base) + (uint32_t)kb * 16384u + 32u * (uint32_t)g0;
+                                        for (int k = 0; k < cnt; ++k) {
+                                            if (part == 0) {
+                                                mma_ts<MODE>(dcol, a_op + 8u * k, bk + 2u * k, id, k == 0 ? acc : 1u);
+                                                mma_f16(dcol, smem_desc(alo_k + 32u * k), bk + 2u * k, id, 1u);
+                                            } else {
+                                                mma_ts<MODE>(dcol, a_op + 8u * k, bk + 2u * k, id, 1u);
+                                            }
+                                        }
+                                    } else if (PARTS == 2 && cnt == 4) {
                                         mma_k4x2(dcol, a_op, a_lo + acol, bk, id, acc);   // A_hi B_hi + A_lo B_hi
                                         mma_k4<MODE>(dcol, a_op, bd_lo + goff, id, 1u);  // A_hi B_lo
                                     } else if (cnt == 4) {
@@ -695,9 +730,10 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                         mbar_arrive(smem_u32(&empty_bar[s]));
                         if (++s == (uint32_t)P.n_stages) { s = 0; ph ^= 1; }
                         int rest = sb_n - 1;
-                        for (int l2 = l + 1; l2 <= Dt; ++l2) rest += ((W + UPS - 1) / UPS + KBS - 1) / KBS;
+                        for (int l2 = l + 1; l2 <= Dt; ++l2)
+                            rest += ALO ? 2 * ((W + UPS - 1) / UPS) : ((W + UPS - 1) / UPS + KBS - 1) / KBS;
                         for (int k = 0; k < rest && ok; ++k) {
-                            ok = mbar_wait(smem_u32(&full_bar[s]), ph, abort, hdr, 9, true);
+                            ok = mbar_wait(smem_u32(&full_bar[s]), ph, abort, hdr, 9, true, P.wait_ns);
                             if (!ok) break;
                             mbar_arrive(smem_u32(&empty_bar[s]));
                             if (++s == (uint32_t)P.n_stages) { s = 0; ph ^= 1; }
@@ -724,11 +760,14 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
         const int r = q * 32 + lane;            // tile row
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
         const uint32_t t_lane = tmem + lane_off;
-        const uint32_t a_hi_l = a_hi + lane_off, a_lo_l = a_lo + lane_off;
+        const uint32_t a_hi_l = a_hi + lane_off;
+        // ALO: this row's address in the first A_lo tile in shared memory; else its TMEM lane
+        const uint32_t a_lo_l = ALO ? smem_u32(alo_base) + (uint32_t)r * 128u : a_lo + lane_off;
         uint32_t pd = 0, px = 0;
         bool ok = true;
         auto signal = [&](uint64_t *bar, bool after_st) {  // this warp's share is done
             if (after_st) tmem_wait_st();
+            if (ALO && after_st) fence_async_smem();  // the A_lo stores -> visible to the tensor core
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(bar));
@@ -737,13 +776,15 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
         // partial dot products, slice 0 adds them to its own.
         auto exchange = [&](float &sa, float &sb) {
             if (slice != 0) {
-                ok = mbar_wait(smem_u32(x_empty), px ^ 1, abort, hdr, 6, false) && ok;
+                ok = mbar_wait(smem_u32(x_empty), px ^ 1, abort, hdr, 6, false, P.wait_ns) && ok;
+                ok = __all_sync(0xffffffffu, ok);
                 px ^= 1;
                 tailx[(slice - 1) * 256 + r] = sa;
                 if (MULT) tailx[(slice - 1) * 256 + 128 + r] = sb;
                 mbar_arrive(smem_u32(x_full));
             } else {
-                ok = mbar_wait(smem_u32(x_full), px, abort, hdr, 7, false) && ok;
+                ok = mbar_wait(smem_u32(x_full), px, abort, hdr, 7, false, P.wait_ns) && ok;
+                ok = __all_sync(0xffffffffu, ok);
                 px ^= 1;
 #pragma unroll
                 for (int k = 0; k < kSlices - 1; ++k) {
@@ -766,7 +807,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                 for (int i = 0; i < 4; ++i) pack2<MODE>(h8[2 * i], h8[2 * i + 1], phi[i], plo[i]);
                 asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_hi_l + (uint32_t)(c0 >> 1)),
                              "r"(phi[0]), "r"(phi[1]), "r"(phi[2]), "r"(phi[3]));
-                if (MODE == TC_SPLIT16)
+                if (MODE == TC_SPLIT16 && !ALO)  // (ALO serves raw-coordinate models only: no Fourier layer 1)
                     asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_lo_l + (uint32_t)(c0 >> 1)),
                                  "r"(plo[0]), "r"(plo[1]), "r"(plo[2]), "r"(plo[3]));
             }
@@ -896,7 +937,8 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             }
             // ---- tensor-core layers
             for (int l = P.first_mma; l <= Dt && ok; ++l) {
-                ok = mbar_wait(smem_u32(d_full), pd, abort, hdr, 4, false) && ok;
+                ok = mbar_wait(smem_u32(d_full), pd, abort, hdr, 4, false, P.wait_ns) && ok;
+                ok = __all_sync(0xffffffffu, ok);  // the TMEM loads below are warp-collective
                 pd ^= 1;
                 if (!ok) break;
                 tc_fence_after();
@@ -913,7 +955,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                             uint32_t v[16];
                             tmem_ld16(t_lane + (uint32_t)c0, v);
                             tmem_wait_ld();
-                            epilogue16<MODE, ACT, TAIL, GRAD>(cs, W, c1, v, c0, !last, a_hi_l, a_lo_l, sa, sb, is_val, P.finer_k);
+                            epilogue16<MODE, ACT, TAIL, GRAD, ALO>(cs, W, c1, v, c0, !last, a_hi_l, a_lo_l, sa, sb, is_val, P.finer_k);
                         }
                         if (!last && !dyn) signal(&a_ready[kb], true);
                     }
@@ -927,16 +969,16 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
 #pragma unroll
                     for (int kb = 1; kb < 4; ++kb)
                         if (kb < KB) tmem_ld32(t_lane + (uint32_t)(64 * kb + su0), v[kb]);
-                    epilogue16<MODE, ACT, TAIL, GRAD>(cs, W, c1, v[0], su0, !last, a_hi_l, a_lo_l, sa, sb, is_val, P.finer_k);
-                    epilogue16<MODE, ACT, TAIL, GRAD>(cs, W, c1, v[0] + 16, su0 + 16, !last, a_hi_l, a_lo_l, sa, sb, is_val, P.finer_k);
+                    epilogue16<MODE, ACT, TAIL, GRAD, ALO>(cs, W, c1, v[0], su0, !last, a_hi_l, a_lo_l, sa, sb, is_val, P.finer_k);
+                    epilogue16<MODE, ACT, TAIL, GRAD, ALO>(cs, W, c1, v[0] + 16, su0 + 16, !last, a_hi_l, a_lo_l, sa, sb, is_val, P.finer_k);
                     tmem_wait_ld();
                     signal(d_drained, false);  // the next layer may overwrite the accumulator
                     if (!last && !dyn) signal(&a_ready[0], true);
 #pragma unroll
                     for (int kb = 1; kb < 4; ++kb) {
                         if (kb < KB) {
-                            epilogue16<MODE, ACT, TAIL, GRAD>(cs, W, c1, v[kb], 64 * kb + su0, !last, a_hi_l, a_lo_l, sa, sb, is_val, P.finer_k);
-                            epilogue16<MODE, ACT, TAIL, GRAD>(cs, W, c1, v[kb] + 16, 64 * kb + su0 + 16, !last, a_hi_l,
+                            epilogue16<MODE, ACT, TAIL, GRAD, ALO>(cs, W, c1, v[kb], 64 * kb + su0, !last, a_hi_l, a_lo_l, sa, sb, is_val, P.finer_k);
+                            epilogue16<MODE, ACT, TAIL, GRAD, ALO>(cs, W, c1, v[kb] + 16, 64 * kb + su0 + 16, !last, a_hi_l,
                                                               a_lo_l, sa, sb, is_val, P.finer_k);
                             if (!last && !dyn) signal(&a_ready[kb], true);
                         }
@@ -988,6 +1030,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                 }
             }
         }
+        cp_async_wait_all();  // after an abort a prefetched row copy may still be in flight
     } else if (CCW && cc_on) {
         // ------------------------------------------------ CUDA-core warps: exit-layer-1 rows
         // Each thread takes eight rows at a time (r + 64 k of a 512-row step; steps strided over

@@ -26,8 +26,9 @@ static int mode_of(int precision) {
 bool tc_supported(const sand_tmlp_desc &d, int precision) {
     if (mode_of(precision) < 0) return false;
     if (d.width != 64 && d.width != 128 && d.width != 256 && d.width != 336) return false;
-    // width 336: the accumulator (336 columns) plus one fp16 operand (168) fill TMEM; no room for the float32 split
-    if (d.width == 336 && mode_of(precision) == TC_SPLIT16) return false;
+    // width 336 in the float32 split: the accumulator (336 columns) plus the hi operand (168) fill TMEM, so the lo
+    // operand goes to shared memory (kernel variant kAloVar), which serves raw-coordinate models only
+    if (d.width == 336 && mode_of(precision) == TC_SPLIT16 && d.encoder != SAND_ENC_NONE) return false;
     if (d.encoder == SAND_ENC_FOURIER && d.in_dim != d.width) return false;
     // FP8 stores the activations unscaled, which holds for the sine's [-1, 1] only
     if (mode_of(precision) == TC_FP8 && d.activation == SAND_ACT_RELU) return false;  // |h| <= 1 only for sines
@@ -53,8 +54,9 @@ struct TcPack {
 };
 
 size_t tc_smem_bytes(const TcParams &P, int parts) {
-    (void)parts;  // the A operand lives in TMEM
-    return 1024 /*alignment slack*/ + (size_t)P.n_stages * P.stage_bytes +
+    (void)parts;  // the A operand lives in TMEM (its lo part in shared memory when P.alo)
+    const size_t alo = P.alo ? (size_t)((P.W + 63) / 64) * 16384 : 0;
+    return 1024 /*alignment slack*/ + alo + (size_t)P.n_stages * P.stage_bytes +
            (size_t)4 * 3 * P.L * P.W /*per-layer constants*/ + kMiscBytes;
 }
 
@@ -237,12 +239,14 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
     P.first_mma = first;
     P.finer_k = d.activation == SAND_ACT_FINER ? (float)(1.0 / (double)d.omega0) : 0.f;
     P.kpad = kpad;
-    P.stage_bytes = 2u * (uint32_t)W * 128u;  // hi and lo of one K-block, or two K-blocks of the one-part modes
+    P.alo = (mode == TC_SPLIT16 && W > 256) ? 1 : 0;
+    // hi and lo of one K-block, or two K-blocks of the one-part modes; with A_lo in shared memory one part
+    P.stage_bytes = (P.alo ? 1u : 2u) * (uint32_t)W * 128u;
     P.box_rows = box_rows;
     P.n_split = W <= 256 ? W : 176;
     {   // accumulator (W columns) + A_hi (W/2; FP8: ceil32(W)/4) [+ A_lo (W/2)], rounded up to a power of two
         const uint32_t a_cols = fp8 ? (uint32_t)((W + 31) / 32 * 8) : (uint32_t)(W / 2);
-        uint32_t need = (uint32_t)W + (uint32_t)parts * a_cols, cols = 32;
+        uint32_t need = (uint32_t)W + (uint32_t)(P.alo ? 1 : parts) * a_cols, cols = 32;
         while (cols < need) cols <<= 1;
         P.tmem_cols = cols;
     }
@@ -273,7 +277,7 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
 
 cudaError_t launch_tmlp_tc(const TcModel &tc, const TmlpDev &M, const float *pts, int64_t n, int full_depth, void *ws,
                            float *out, int num_sms, cudaStream_t s, int all_tails, float dyn_r, uint8_t *exit_out,
-                           float *grad) {
+                           float *grad, uint64_t wait_ns) {
     (void)M;
     TcPack *pk = static_cast<TcPack *>(tc.host);
     if (!pk) return cudaErrorInvalidValue;
@@ -282,6 +286,7 @@ cudaError_t launch_tmlp_tc(const TcModel &tc, const TmlpDev &M, const float *pts
     P.dyn_r = full_depth && !P.all_tails ? dyn_r : 0.f;
     P.exit_out = P.dyn_r > 0.f ? exit_out : nullptr;
     P.grad = P.all_tails || P.dyn_r > 0.f ? nullptr : grad;
+    P.wait_ns = wait_ns ? wait_ns : kTimeoutNs;
     WsLayout Lw = ws_layout(full_depth ? 0 : n);
     char *base = static_cast<char *>(ws);
     WsHeader *hdr = reinterpret_cast<WsHeader *>(base);
@@ -292,7 +297,18 @@ cudaError_t launch_tmlp_tc(const TcModel &tc, const TmlpDev &M, const float *pts
     const int64_t tiles = (n + ppt - 1) / ppt;
     int grid = num_sms;
     if (tiles < grid) grid = (int)(tiles > 0 ? tiles : 1);
-    const int var = P.grad ? 2 : (P.all_tails || P.dyn_r > 0.f) ? 1 : (!full_depth && P.cc) ? 3 : 0;
+    const int var = (P.grad ? 2 : (P.all_tails || P.dyn_r > 0.f) ? 1 : (!full_depth && P.cc) ? 3 : 0) |
+                    (P.alo ? kAloVar : 0);
+#define SAND_ARGS pk->map, P, P.act, P.tail_kind, pts, sorted, hdr, n, full_depth, out, grid, smem, s
+    if (pk->mode == TC_SPLIT16 && (var & kAloVar)) {
+        switch (var & 3) {
+            case 3: return launch_tc_mode<TC_SPLIT16, 7>(SAND_ARGS);
+            case 2: return launch_tc_mode<TC_SPLIT16, 6>(SAND_ARGS);
+            case 1: return launch_tc_mode<TC_SPLIT16, 5>(SAND_ARGS);
+            default: return launch_tc_mode<TC_SPLIT16, 4>(SAND_ARGS);
+        }
+    }
+#undef SAND_ARGS
 #define SAND_LAUNCH(M)                                                                                                  \
     (var == 3   ? launch_tc_mode<M, 3>(pk->map, P, P.act, P.tail_kind, pts, sorted, hdr, n, full_depth, out, grid, smem, s) \
      : var == 2 ? launch_tc_mode<M, 2>(pk->map, P, P.act, P.tail_kind, pts, sorted, hdr, n, full_depth, out, grid, smem, s) \

@@ -260,7 +260,7 @@ sand_status sand_sphere_trace(sand_model m, const float *d_origin, int per_ray_o
     if (mis & 3) { set_error("device buffers must be 4-byte aligned"); return SAND_EINVAL; }
     sand_query_opts q{};
     if (qopts) q = *qopts;
-    if (q.full_depth || q.d_exit_layers || q.d_workspace || q.stage_events) {
+    if (q.full_depth || q.d_exit_layers || q.d_workspace || q.stage_events || q.wait_limit_us) {
         set_error("trace queries take only precision and max_depth from the query options");
         return SAND_EINVAL;
     }

@@ -51,18 +51,20 @@ def test_every_declared_symbol_is_exported(L):
 def test_struct_layouts_match_binding(tmp_path):
     from paper_2604_25936_gb300 import binding
     prog = tmp_path / "sizes.c"
-    prog.write_text('#include "sand.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
+    prog.write_text('#include "sand.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
                     'sizeof(sand_tmlp_desc), sizeof(sand_depth_map_desc), sizeof(sand_query_opts),'
                     'sizeof(sand_query_stats), offsetof(sand_query_opts, d_workspace), offsetof(sand_tmlp_desc, omega0),'
                     'sizeof(sand_trace_opts), offsetof(sand_trace_opts, poll_every), sizeof(sand_map_build_opts),'
-                    'sizeof(sand_train_opts), offsetof(sand_train_opts, eps));return 0;}\n')
+                    'sizeof(sand_train_opts), offsetof(sand_train_opts, eps), sizeof(sand_server_report),'
+                    'offsetof(sand_server_report, batch_ms_sum));return 0;}\n')
     exe = tmp_path / "sizes"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(binding.TmlpDesc), ctypes.sizeof(binding.DepthMapDesc), ctypes.sizeof(binding.QueryOpts),
             ctypes.sizeof(binding.QueryStats), binding.QueryOpts.d_workspace.offset, binding.TmlpDesc.omega0.offset,
             ctypes.sizeof(binding.TraceOpts), binding.TraceOpts.poll_every.offset, ctypes.sizeof(binding.MapBuildOpts),
-            ctypes.sizeof(binding.TrainOpts), binding.TrainOpts.eps.offset]
+            ctypes.sizeof(binding.TrainOpts), binding.TrainOpts.eps.offset, ctypes.sizeof(binding.ServerReport),
+            binding.ServerReport.batch_ms_sum.offset]
     assert got == want
 
 

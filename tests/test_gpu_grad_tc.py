@@ -71,11 +71,14 @@ def model_of(kind):
         return synth.siren_tmlp(8, 256, seed=1, tail_kind=synth.TAIL_MULT), synth.scene_octree(7, 8, far_field=True)
     if kind == "siren_w64":
         return synth.siren_tmlp(4, 64, seed=2), synth.scene_octree(6, 4, far_field=True)
+    if kind == "siren_w336":
+        return synth.siren_tmlp(8, 336, seed=2), synth.scene_octree(7, 8, transform=synth.rotation([0, 1, 0], 0.5),
+                                                                    scale=0.95)
     return synth.relu_ff_tmlp(6, 128, n_freq=64, sigma=10.0, seed=3), synth.scene_octree(7, 6)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
-@pytest.mark.parametrize("kind", ["siren", "siren_mult", "siren_w64", "relu_ff"])
+@pytest.mark.parametrize("kind", ["siren", "siren_mult", "siren_w64", "siren_w336", "relu_ff"])
 def test_tc_gradient_parity(kind, prec):
     """SAND queries (depth map, binned by exit layer, tiles straddling two bins, a ragged last
     tile of 6001 or 20001 mod 32 points) against the oracle value and gradient."""
