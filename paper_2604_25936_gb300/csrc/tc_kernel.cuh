@@ -10,8 +10,11 @@
 //                D[128 x W] (fp32, TMEM) += A[128 x 16] . B[W x 16]^T, A read from TMEM.
 //   warps 2..9   epilogue.  Thread (quadrant q, lane i) owns tile row 32 q + i (the
 //                TMEM lane restriction); the two warps of a quadrant take half of the
-//                units of every K-block each.  Layer 1's operand (the split coordinates
-//                of one K = 16 MMA), bias, sine, tails, the running sum
+//                units of every K-block each.  Layer 1 of raw coordinates with linear
+//                tails entirely on the CUDA cores (W1' x + b1' from the row's coordinates
+//                and weights in shared memory; the tensor cores start at layer 2);
+//                otherwise layer 1's A operand (the split coordinates of one K = 16 MMA,
+//                or the Fourier features).  Then bias, sine, tails, the running sum
 //                y_l = y_{l-1} + t_l and the write at each row's exit layer.  The new
 //                activations are packed (fp16 pair, bf16 or e4m3) and written with
 //                tcgen05.st into TMEM, where the next layer's MMAs read them as the A
@@ -188,6 +191,11 @@ __device__ __forceinline__ void cp_async4(uint32_t dst, const void *src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ float4 lds_f4(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+    return v;
+}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -405,19 +413,27 @@ __device__ __forceinline__ void tmem_st_half(uint32_t taddr, const uint32_t *v) 
 // FINER: cos(p) (1 + 2 |u| k) du with p = u + u |u| k its phase.
 // ALO: a_lo is the shared-memory address of this row in the first 16 KB K-block tile of the A_lo
 // operand (128-byte rows, 128-byte swizzle, tiles 1024-byte aligned), not a TMEM address.
-template <int MODE, int ACT, int TAIL, bool GRAD = false, bool ALO = false>
+// L1: layer 1 of raw coordinates instead, its phase straight from the row's coordinates (x0, x1,
+// x2) and s (W1, b1) of every unit, read from shared memory at w1s (three float32 FMAs per unit,
+// as on the CUDA-core warps); v and the bias constants unused.
+template <int MODE, int ACT, int TAIL, bool GRAD = false, bool ALO = false, bool L1 = false>
 __device__ __forceinline__ void epilogue16(const float *cs, int W, float c1, const uint32_t *v, int c0, bool write_a,
-                                           uint32_t a_hi, uint32_t a_lo, float &sa, float &sb, bool is_val, float fk) {
-    constexpr bool MULT = TAIL == SAND_TAIL_MULT;
+                                           uint32_t a_hi, uint32_t a_lo, float &sa, float &sb, bool is_val, float fk,
+                                           uint32_t w1s = 0, float x0 = 0.f, float x1 = 0.f, float x2 = 0.f) {
+    constexpr bool MULT = TAIL == SAND_TAIL_MULT && !L1;  // tail 1 is affine for both tail kinds
     uint32_t phi[8], plo[8], p8[4];
 #pragma unroll
     for (int g = 0; g < 2; ++g) {
         const int j0 = c0 + 8 * g;
-        const float4 ba = *reinterpret_cast<const float4 *>(cs + j0);
-        const float4 bb = *reinterpret_cast<const float4 *>(cs + j0 + 4);
+        float bv[8];
+        if (!L1) {
+            const float4 ba = *reinterpret_cast<const float4 *>(cs + j0);
+            const float4 bb = *reinterpret_cast<const float4 *>(cs + j0 + 4);
+            bv[0] = ba.x; bv[1] = ba.y; bv[2] = ba.z; bv[3] = ba.w;
+            bv[4] = bb.x; bv[5] = bb.y; bv[6] = bb.z; bv[7] = bb.w;
+        }
         const float4 aa = *reinterpret_cast<const float4 *>(cs + W + j0);
         const float4 ab4 = *reinterpret_cast<const float4 *>(cs + W + j0 + 4);
-        const float bv[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
         const float av[8] = {aa.x, aa.y, aa.z, aa.w, ab4.x, ab4.y, ab4.z, ab4.w};
         float tbv[8];
         if (MULT) {
@@ -430,7 +446,10 @@ __device__ __forceinline__ void epilogue16(const float *cs, int W, float c1, con
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             float hv;
-            if (!GRAD) {
+            if (L1) {
+                const float4 w = lds_f4(w1s + 16u * (uint32_t)(j0 + i));
+                hv = activate<ACT>(fmaf(w.x, x0, fmaf(w.y, x1, fmaf(w.z, x2, w.w))), fk);
+            } else if (!GRAD) {
                 hv = activate<ACT>(fmaf(__uint_as_float(v[8 * g + i]), c1, bv[i]), fk);
             } else {
                 const float u = fmaf(__uint_as_float(v[8 * g + i]), c1, is_val ? bv[i] : 0.f);
@@ -500,8 +519,13 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
     const int KBP = (W + 63) >> 6;  // K-blocks of the A_lo operand in shared memory (ALO)
     uint8_t *alo_base = smem;
     uint8_t *stage_base = smem + (ALO ? (size_t)KBP * 16384 : 0);
-    float *c_all = reinterpret_cast<float *>(stage_base + (size_t)P.n_stages * P.stage_bytes);  // [L][3][W]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(c_all + (size_t)3 * L * W);
+    // per-layer constants [L][NC][W]: bias', tail a (and tail b with multiplicative tails), then, for a
+    // raw-coordinate layer 1 with linear tails, s (W1, b1) of every unit ([W] float4)
+    constexpr int NC = MULT ? 3 : 2;
+    const bool w1_smem = P.l1_fold && !MULT;
+    float *c_all = reinterpret_cast<float *>(stage_base + (size_t)P.n_stages * P.stage_bytes);
+    float4 *w1s = reinterpret_cast<float4 *>(c_all + (size_t)NC * L * W);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(w1s + (w1_smem ? W : 0));
     uint64_t *full_bar = bars;
     uint64_t *empty_bar = bars + kMaxStages;
     uint64_t *a_ready = bars + 2 * kMaxStages;  // [kb]: K-block kb of the next A operand is in TMEM (16 warps)
@@ -529,6 +553,11 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
     const int64_t n_tc_rows = cc_on ? (int64_t)hdr->bin_start[1] : n_rows;  // tensor-core rows
     const int64_t n_tiles = (n_tc_rows + PPT - 1) / PPT;
     auto tile_depth = [&](int64_t t) -> int { return full_depth ? L : tc_row_depth(s_bin, (uint32_t)(t * PPT), L); };
+    // Layer 1 of raw coordinates (linear tails) runs on the epilogue warps' CUDA cores (three FMAs
+    // per unit from the coordinates, no MMA and no accumulator drain), except in the gradient
+    // variant, which keeps the folded K = 16 MMA; the tensor cores then start at layer 2.
+    const bool l1cc = !GRAD && w1_smem;
+    const int l_mma0 = l1cc ? 2 : P.first_mma;  // first layer on the tensor cores
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < P.n_stages; ++s) {
@@ -553,7 +582,12 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (warp >= 2 && warp < 2 + kEpiWarps) {  // constants of every layer, resident for the whole kernel
-        for (int i = threadIdx.x - 64; i < 3 * L * W; i += kEpiThreads) c_all[i] = __ldg(P.cvec + i);
+        for (int i = threadIdx.x - 64; i < NC * L * W; i += kEpiThreads) {
+            const int l = i / (NC * W), c = (i / W) % NC, j = i % W;
+            c_all[i] = __ldg(P.cvec + ((size_t)l * 3 + c) * W + j);
+        }
+        if (w1_smem)
+            for (int j = threadIdx.x - 64; j < W; j += kEpiThreads) w1s[j] = __ldg(P.w1p + j);
     }
     tc_fence_before();
     __syncthreads();
@@ -568,7 +602,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             bool ok = true;
             for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
                 const int Dt = tile_depth(t);
-                for (int l = P.first_mma; l <= Dt && ok; ++l) {
+                for (int l = l_mma0; l <= Dt && ok; ++l) {
                     const int kb_n = ((l == 1 ? P.D : W) + UPS - 1) / UPS;
                     const bool fold_l = l == 1 && P.l1_fold;
                     const int parts_l = fold_l ? 1 : PARTS;  // the folded layer 1 has one block
@@ -628,7 +662,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
                 const int Dt = tile_depth(t);
                 bool tile_skip = false;
-                for (int l = P.first_mma; l <= Dt && ok && !tile_skip; ++l) {
+                for (int l = l_mma0; l <= Dt && ok && !tile_skip; ++l) {
                     const int K = l == 1 ? P.D : W;
                     const int kb_n = (K + UPS - 1) / UPS;
                     const int ks_n = (K + UPK - 1) / UPK;  // the last FP8 K-step may be half zero padding
@@ -899,6 +933,19 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             }
             put_a1(a1);
         };
+        // Layer 1 of raw coordinates on the CUDA cores (l1cc): this thread's units of every K-block,
+        // written (write_a) as the A operand of layer 2 one K-block at a time, each K-block
+        // released to the MMAs as it is done (sig); returns this thread's partial sum of tail 1.
+        auto layer1 = [&](const TcRow &a, bool write_a, bool sig) -> float {
+            float s1 = 0.f, s1b = 0.f;
+            for (int kb = 0; kb < KB; ++kb) {
+                for (int c0 = 64 * kb + su0; c0 < 64 * kb + su0 + kSliceUnits && c0 < W; c0 += 16)
+                    epilogue16<MODE, ACT, TAIL, false, ALO, true>(c_all, W, 0.f, nullptr, c0, write_a, a_hi_l, a_lo_l, s1, s1b,
+                                                                  true, P.finer_k, smem_u32(w1s), a.x0, a.x1, a.x2);
+                if (write_a && sig) signal(&a_ready[kb], true);
+            }
+            return s1;
+        };
         int buf = 0;
         prefetch_row(blockIdx.x, 0);
         for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, buf ^= 1) {
@@ -910,8 +957,40 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             const float x0 = cur.x0, x1 = cur.x1, x2 = cur.x2;
             float y = 0.f;
             bool alive = idx >= 0;  // dynamic exit: this row still runs
-            // ---- the A operand of layer 1: split coordinates, or the Fourier features
-            if (P.l1_fold) {
+            // ---- layer 1 on the CUDA cores; or the A operand of layer 1: split coordinates, or the
+            // Fourier features
+            int l_end = Dt;  // last layer of this tile on the tensor cores
+            if (l1cc) {
+                const bool dyn = EXT && P.dyn_r > 0.f;
+                const bool more = Dt >= 2;
+                float s1 = layer1(cur, more, more && !dyn);
+                float s1b = 0.f;
+                exchange(s1, s1b);
+                if (slice == 0) {
+                    y = s1 + __ldg(P.tb);  // tail 1 (affine for both tail kinds)
+                    if (dyn) {
+                        if (alive && (fabsf(y) < P.dyn_r || !more)) {  // the row stops here
+                            out[idx] = y;
+                            if (P.exit_out) P.exit_out[idx] = (uint8_t)1;
+                            alive = false;
+                        }
+                    } else if (EXT && P.all_tails) {
+                        if (idx >= 0) out[idx * L] = y;
+                    } else if (d == 1 && idx >= 0) {
+                        out[idx] = y;
+                    }
+                }
+                if (dyn && more) {  // as after every layer below: go on, or skip the rest of the tile
+                    const int n_alive = named_count(1, kEpiThreads, slice == 0 && alive);
+                    if (n_alive > 0) {
+                        for (int kb = 0; kb < KB; ++kb) signal(&a_ready[kb], true);
+                    } else {
+                        if (threadIdx.x == 64) *skip = 1;
+                        signal(&a_ready[0], true);
+                        l_end = 0;
+                    }
+                }
+            } else if (P.l1_fold) {
                 put_a1_row(cur);
             } else {
                 // Fourier features gamma(x) = [sin 2 pi s, cos 2 pi s]; in_dim == W, same slices as the layers
@@ -936,7 +1015,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                 }
             }
             // ---- tensor-core layers
-            for (int l = P.first_mma; l <= Dt && ok; ++l) {
+            for (int l = l_mma0; l <= l_end && ok; ++l) {
                 ok = mbar_wait(smem_u32(d_full), pd, abort, hdr, 4, false, P.wait_ns) && ok;
                 ok = __all_sync(0xffffffffu, ok);  // the TMEM loads below are warp-collective
                 pd ^= 1;
@@ -944,7 +1023,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                 tc_fence_after();
                 const bool last = l == Dt;
                 const bool dyn = EXT && P.dyn_r > 0.f;
-                const float *cs = c_all + (size_t)(l - 1) * 3 * W;
+                const float *cs = c_all + (size_t)(l - 1) * NC * W;
                 const float c1 = P.c1[l - 1];
                 float sa = 0.f, sb = 0.f;
                 if (!drain_first) {
@@ -1062,7 +1141,8 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             for (int k = 0; k < kCcRows; ++k) s[k] = 0.f;
 #pragma unroll 4
             for (int j = 0; j < W; ++j) {
-                const float4 w = __ldg(P.w1p + j);  // the same unit in every lane: one broadcast
+                // the same unit in every lane: one broadcast (from shared memory with linear tails)
+                const float4 w = MULT ? __ldg(P.w1p + j) : lds_f4(smem_u32(w1s + j));
                 const float a = ta[j];
 #pragma unroll
                 for (int k = 0; k < kCcRows; ++k)

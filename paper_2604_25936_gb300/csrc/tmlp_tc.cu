@@ -56,8 +56,10 @@ struct TcPack {
 size_t tc_smem_bytes(const TcParams &P, int parts) {
     (void)parts;  // the A operand lives in TMEM (its lo part in shared memory when P.alo)
     const size_t alo = P.alo ? (size_t)((P.W + 63) / 64) * 16384 : 0;
-    return 1024 /*alignment slack*/ + alo + (size_t)P.n_stages * P.stage_bytes +
-           (size_t)4 * 3 * P.L * P.W /*per-layer constants*/ + kMiscBytes;
+    const bool mult = P.tail_kind == SAND_TAIL_MULT;
+    const size_t consts = (size_t)4 * (mult ? 3 : 2) * P.L * P.W;          // per-layer constants
+    const size_t w1 = P.l1_fold && !mult ? (size_t)16 * P.W : 0;           // raw-coordinate layer 1
+    return 1024 /*alignment slack*/ + alo + (size_t)P.n_stages * P.stage_bytes + consts + w1 + kMiscBytes;
 }
 
 sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params, int precision) {
