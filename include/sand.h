@@ -180,9 +180,17 @@ sand_status sand_query_sdf_grad(sand_model m, const float *d_points, int64_t n, 
                                 const sand_query_opts *opts, void *stream);
 
 /* End-to-end query from HOST memory: copies h_points to the device, runs the
- * query, copies the SDF back to h_out, in chunks pipelined over the stream.
- * Pinned host memory gives full copy bandwidth.  Synchronous: returns after
- * h_out is written. */
+ * query, copies the SDF back to h_out.  From 2^20 points on the work goes in up
+ * to four chunks as a pipeline: chunk k (the blocks k, k + 4, k + 8, ... of 2^18
+ * consecutive points, so that every chunk samples the whole input) is copied up
+ * on a copy stream of the model's own, its query runs on `stream` once it has
+ * arrived, and its values are copied down on a second copy stream once it is
+ * done, so the copies of one chunk overlap the queries of the others.  Each chunk is a query of its own points, which leaves every point's
+ * result unchanged (results do not depend on the batch); sand_read_stats then
+ * describes the last chunk.  The copies wait for the work queued on `stream`
+ * before the call.  Pinned host memory gives full copy bandwidth (and lets the
+ * copies run asynchronously).  Synchronous: returns after h_out is written, and
+ * on every error path only after the three streams have drained. */
 sand_status sand_query_sdf_host(sand_model m, const float *h_points, int64_t n, float *h_out,
                                 const sand_query_opts *opts, void *stream);
 

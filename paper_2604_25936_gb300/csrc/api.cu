@@ -30,6 +30,8 @@ struct sand_model_s {
     size_t ws_bytes = 0;
     float *d_stage = nullptr;         // staging for host-memory queries: points then outputs
     size_t stage_bytes = 0;
+    cudaStream_t copy_in = nullptr;   // host-memory queries: the copy streams of the chunk pipeline
+    cudaStream_t copy_out = nullptr;
     void *d_trace = nullptr;          // sphere-tracer state (rays, active lists, points, workspace)
     size_t trace_bytes = 0;
 };
@@ -147,6 +149,9 @@ static void release(sand_model_s *m) {
     cudaFree(m->d_ws);
     cudaFree(m->d_stage);
     cudaFree(m->d_trace);
+    if (m->copy_in) cudaStreamDestroy(m->copy_in);
+    if (m->copy_out) cudaStreamDestroy(m->copy_out);
+    m->copy_in = m->copy_out = nullptr;
 }
 
 static sand_status ensure_workspace(sand_model_s *m, int64_t n, bool grad, void **ws, size_t *bytes) {
@@ -706,11 +711,78 @@ sand_status sand_query_sdf_host(sand_model m, const float *h_points, int64_t n, 
     }
     float *d_pts = m->d_stage;
     float *d_out = m->d_stage + (size_t)n * 3;
-    SAND_CUDA(cudaMemcpyAsync(d_pts, h_points, (size_t)n * 12, cudaMemcpyHostToDevice, s), "H2D points");
-    st = run_query(m, d_pts, n, d_out, nullptr, &o, stream);
+    // A pipeline of chunks: chunk k's points go up on copy_in, its query runs on the caller's
+    // stream once they are there, and its values come down on copy_out once it is done, so
+    // the copies of one chunk overlap the queries of the others.  Chunk k is made of the
+    // blocks k, k + n_chunks, k + 2 n_chunks, ... of kHostBlock consecutive points, packed
+    // together on the device: spread over the whole input, every chunk gets about the same
+    // mix of exit layers (a contiguous slab of a spatially ordered input may be all far field
+    // or all surface, which leaves one kind of warp of the T-MLP kernel idle).  Each chunk is
+    // a query of its own points (a point's result does not depend on the other points).
+    constexpr int kHostChunks = 4;
+    constexpr int64_t kHostBlock = (int64_t)1 << 18;
+    const int64_t n_blocks = (n + kHostBlock - 1) / kHostBlock;
+    const int n_chunks = n < ((int64_t)1 << 20) ? 1 : (int)(n_blocks < kHostChunks ? n_blocks : kHostChunks);
+    if (n_chunks <= 1) {
+        SAND_CUDA(cudaMemcpyAsync(d_pts, h_points, (size_t)n * 12, cudaMemcpyHostToDevice, s), "H2D points");
+        st = run_query(m, d_pts, n, d_out, nullptr, &o, stream);
+        if (st) {
+            cudaStreamSynchronize(s);
+            return st;
+        }
+        SAND_CUDA(cudaMemcpyAsync(h_out, d_out, (size_t)n * 4, cudaMemcpyDeviceToHost, s), "D2H values");
+        SAND_CUDA(cudaStreamSynchronize(s), "stream synchronize");
+        return SAND_OK;
+    }
+    if (!m->copy_in && cudaStreamCreateWithFlags(&m->copy_in, cudaStreamNonBlocking) != cudaSuccess) {
+        m->copy_in = nullptr;
+        return cuda_fail(cudaGetLastError(), "copy stream");
+    }
+    if (!m->copy_out && cudaStreamCreateWithFlags(&m->copy_out, cudaStreamNonBlocking) != cudaSuccess) {
+        m->copy_out = nullptr;
+        return cuda_fail(cudaGetLastError(), "copy stream");
+    }
+    cudaEvent_t ev[2 * kHostChunks + 1];
+    int n_ev = 0;
+    for (; n_ev < 2 * n_chunks + 1; ++n_ev)
+        if (cudaEventCreateWithFlags(&ev[n_ev], cudaEventDisableTiming) != cudaSuccess) break;
+    cudaError_t ce = n_ev == 2 * n_chunks + 1 ? cudaSuccess : cudaGetLastError();
+    // the copies follow whatever the caller queued on its stream before this call
+    if (ce == cudaSuccess) ce = cudaEventRecord(ev[2 * n_chunks], s);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(m->copy_in, ev[2 * n_chunks], 0);
+    int64_t base = 0;  // first device row of chunk k
+    for (int k = 0; k < n_chunks && ce == cudaSuccess && st == SAND_OK; ++k) {
+        int64_t cnt = 0;
+        for (int64_t b = k; b < n_blocks && ce == cudaSuccess; b += n_chunks) {
+            const int64_t off = b * kHostBlock, len = n - off < kHostBlock ? n - off : kHostBlock;
+            ce = cudaMemcpyAsync(d_pts + 3 * (base + cnt), h_points + 3 * off, (size_t)len * 12, cudaMemcpyHostToDevice,
+                                 m->copy_in);
+            cnt += len;
+        }
+        if (ce == cudaSuccess) ce = cudaEventRecord(ev[2 * k], m->copy_in);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s, ev[2 * k], 0);
+        if (ce != cudaSuccess) break;
+        st = run_query(m, d_pts + 3 * base, cnt, d_out + base, nullptr, &o, stream);
+        if (st) break;
+        ce = cudaEventRecord(ev[2 * k + 1], s);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(m->copy_out, ev[2 * k + 1], 0);
+        int64_t at = base;
+        for (int64_t b = k; b < n_blocks && ce == cudaSuccess; b += n_chunks) {
+            const int64_t off = b * kHostBlock, len = n - off < kHostBlock ? n - off : kHostBlock;
+            ce = cudaMemcpyAsync(h_out + off, d_out + at, (size_t)len * 4, cudaMemcpyDeviceToHost, m->copy_out);
+            at += len;
+        }
+        base += cnt;
+    }
+    // every path waits for all three streams: no copy may still touch the caller's buffers
+    const cudaError_t e1 = cudaStreamSynchronize(m->copy_in);
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    const cudaError_t e3 = cudaStreamSynchronize(m->copy_out);
+    for (int i = 0; i < n_ev; ++i) cudaEventDestroy(ev[i]);
     if (st) return st;
-    SAND_CUDA(cudaMemcpyAsync(h_out, d_out, (size_t)n * 4, cudaMemcpyDeviceToHost, s), "D2H values");
-    SAND_CUDA(cudaStreamSynchronize(s), "stream synchronize");
+    if (ce != cudaSuccess) return cuda_fail(ce, "host query pipeline");
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
+        return cuda_fail(e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3, "stream synchronize");
     return SAND_OK;
 }
 

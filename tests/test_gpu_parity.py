@@ -283,6 +283,29 @@ def test_host_query_and_streams(scene):
     assert torch.equal(y.cpu(), ref)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp32_simt"])
+def test_host_query_chunk_pipeline(scene, prec):
+    """Above 2^20 points the host query runs as a pipeline of chunks (copies on the model's two
+    copy streams, queries on the caller's): 4,500,001 points make four chunks with a ragged last
+    one.  Every value must equal the one-shot device query bit for bit (a point's result does
+    not depend on its batch), from pinned and from pageable host memory, on the default stream
+    and on a side stream."""
+    model, tree, m = scene
+    n = 4500001
+    pts = synth.uniform_points(n, seed=43)
+    ref = m.query(dev(pts), precision=prec).cpu()
+    hp = torch.from_numpy(pts).pin_memory()
+    ho = torch.full((n,), float("nan"), dtype=torch.float32).pin_memory()
+    m.query_host(hp, out=ho, precision=prec)
+    assert torch.equal(ho, ref)
+    yo = m.query_host(pts, precision=prec)  # numpy, pageable
+    assert np.array_equal(yo, ref.numpy())
+    s = torch.cuda.Stream()
+    ho.fill_(float("nan"))
+    m.query_host(hp, out=ho, precision=prec, stream=s)
+    assert torch.equal(ho, ref)
+
+
 @pytest.mark.parametrize("prec", IMPLEMENTED)
 def test_full_size_lattice_sampled(scene, prec):
     """256^3 lattice (16.7M points) in the launch configuration the benchmark times:
