@@ -1,6 +1,8 @@
 // Tensor-core (tcgen05) T-MLP path: packed weights and launcher.
 #pragma once
 
+#include <cuda.h>
+
 #include "internal.cuh"
 
 namespace sand {
@@ -17,6 +19,12 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
 // all_tails (with full_depth): out[i * L + l - 1] = y_l for every layer l of every point.
 // dyn_r > 0 (with full_depth): octree-free dynamic exit at |t_l| < dyn_r, exit layers to exit_out.
 // grad: also dy/dx per point ([n][3], forward-mode tangents as three more rows per point).
+// A 2-D TMA tensor map over rows of `inner` 16-bit elements (row pitch 2 inner bytes), boxes of
+// box_inner x box_rows with the 128-byte swizzle (box_inner x 2 = 128 bytes: one swizzle span).
+// False when the driver entry point or the encoding fails.
+bool encode_u16_rows(CUtensorMap *map, const void *base, uint64_t inner, uint64_t rows, uint32_t box_inner,
+                     uint32_t box_rows);
+
 cudaError_t launch_tmlp_tc(const TcModel &tc, const TmlpDev &M, const float *pts, int64_t n, int full_depth, void *ws,
                            float *out, int num_sms, cudaStream_t s, int all_tails = 0, float dyn_r = 0.f,
                            uint8_t *exit_out = nullptr, float *grad = nullptr, uint64_t wait_ns = 0);

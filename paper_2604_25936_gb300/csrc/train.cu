@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "tc.cuh"
 #include "tc_kernel.cuh"
 
 namespace sand {
@@ -57,9 +58,9 @@ struct TrGemm {
     // A operand: FWD act(a[row][k]); BWD a[row][k]; DW a[k][row]   (ld = a_ld)
     const float *a;
     int a_ld;
-    // B operand: FWD / BWD packed fp16 rows (hi rows then lo rows, bp_ld elements each); DW act(b[k][n])
-    const uint16_t *bp;
-    int bp_ld;
+    // B operand: FWD / BWD packed fp16 rows [hi rows; lo rows] of K elements, loaded by TMA through
+    // the kernel's tensor map from row b_row0 (hi) and b_row0 + N (lo) on; DW act(b[k][n])
+    int b_row0;
     const float *b;
     int b_ld;
     int n_stages;
@@ -138,7 +139,8 @@ __device__ __forceinline__ bool tr_wait_warp(uint32_t bar, uint32_t parity, vola
 }
 
 // One stage of operands (64 K-elements of a 128-row A tile and an N-row B tile) from global memory
-// into shared memory, split into fp16 hi and lo parts, by the kTrProducers producer threads.
+// into shared memory, split into fp16 hi and lo parts, by the kTrProducers producer threads (FWD /
+// BWD: the A tile only; the packed weights come by TMA).
 // Every global load of a group is issued before any of its values is used, so a stage costs a
 // few memory latencies rather than one per chunk.
 template <int EPI>
@@ -159,13 +161,6 @@ __device__ __forceinline__ void tr_produce_stage(const TrGemm &P, int pt, int m0
             va[j][0] = in ? __ldg(src) : make_float4(0.f, 0.f, 0.f, 0.f);
             va[j][1] = in ? __ldg(src + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        // B: the packed fp16 weights (L2-resident), 16-byte asynchronous copies into the swizzled slots
-        for (int it = pt; it < N * 8; it += kTrProducers) {
-            const int r = it >> 3, c = it & 7;
-            cp_async16(bhi + tr_swz(r, c), P.bp + (size_t)r * P.bp_ld + k0 + 8 * c);
-            cp_async16(blo + tr_swz(r, c), P.bp + ((size_t)N + r) * P.bp_ld + k0 + 8 * c);
-        }
-        cp_async_commit();
 #pragma unroll
         for (int j = 0; j < NA; ++j) {
             const int it = pt + j * kTrProducers;
@@ -179,7 +174,6 @@ __device__ __forceinline__ void tr_produce_stage(const TrGemm &P, int pt, int m0
             st_shared_v4(ahi + tr_swz(it >> 3, it & 7), hi);
             st_shared_v4(alo + tr_swz(it >> 3, it & 7), lo);
         }
-        cp_async_wait_all();
     } else {
         // Both operands are [k][row] in memory (rows contiguous).  A quad is four consecutive rows
         // of one chunk: eight float4 loads along the rows, one per K-element, give four chunks.
@@ -232,12 +226,13 @@ __device__ __forceinline__ void tr_produce_stage(const TrGemm &P, int pt, int m0
 
 // Persistent GEMM: CTA b takes tiles b, b + grid, ...; tile t is rows 128 (t % m_tiles) .. + 127
 // and K-blocks of split t / m_tiles.  Two accumulators in TMEM let the epilogue of one tile run
-// while the MMAs of the next one do.
+// while the MMAs of the next one do.  FWD / BWD: the packed weights of a stage (hi and lo) come
+// by two TMA copies (bmap, 128-byte swizzle: the layout tr_swz writes) on their own barrier.
 //   warps 0..3  producers (operands into the shared-memory stage ring)
 //   warp 4      TMEM owner, MMA issuer (one thread)
 //   warps 5..8  epilogue: thread (quadrant warp & 3, lane i) owns tile row 32 (warp & 3) + i
 template <int EPI>
-__global__ void __launch_bounds__(kTrThreads, 1) tr_gemm_kernel(const TrGemm P) {
+__global__ void __launch_bounds__(kTrThreads, 1) tr_gemm_kernel(const __grid_constant__ CUtensorMap bmap, const TrGemm P) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)P.n_stages * P.stage_bytes);
@@ -246,8 +241,13 @@ __global__ void __launch_bounds__(kTrThreads, 1) tr_gemm_kernel(const TrGemm P) 
     uint64_t *acc_full = bars + 2 * kTrMaxStages;   // [2]: an accumulator is complete (commit)
     uint64_t *acc_empty = acc_full + 2;             // [2]: ... and read out (4 epilogue warps)
     uint64_t *drain = acc_empty + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    uint64_t *bfull = drain + 1;                    // [stage]: FWD / BWD: the stage's weights landed (TMA)
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bfull + kTrMaxStages);
     volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    // FWD / BWD epilogue constants of the layer in shared memory: [0, N) bias (FWD), [N, 3N) tail
+    // weights a and b.  Every row reads each of them once per column; through L1 they would miss,
+    // the producers' operand stream evicting them.
+    float *s_c = reinterpret_cast<float *>(tmem_slot + 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int N = P.N;
     const uint32_t a_bytes = kTrBM * 128, b_bytes = (uint32_t)N * 128;
@@ -265,6 +265,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) tr_gemm_kernel(const TrGemm P) 
     if (threadIdx.x == 0) {
         for (int s = 0; s < P.n_stages; ++s) {
             mbar_init(smem_u32(&full[s]), kTrProducers);
+            mbar_init(smem_u32(&bfull[s]), 1);
             mbar_init(smem_u32(&empty[s]), 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -281,6 +282,9 @@ __global__ void __launch_bounds__(kTrThreads, 1) tr_gemm_kernel(const TrGemm P) 
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    if (EPI != TR_DW)
+        for (int i = threadIdx.x; i < 3 * N; i += kTrThreads)
+            s_c[i] = i < N ? (EPI == TR_FWD ? __ldg(P.bias + i) : 0.f) : __ldg(P.tw + (i - N));
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -301,9 +305,24 @@ __global__ void __launch_bounds__(kTrThreads, 1) tr_gemm_kernel(const TrGemm P) 
                     if (!ok) break;
                 }
                 const uint32_t st = smem_u32(smem + (size_t)s * P.stage_bytes);
+                if (EPI != TR_DW && pt == 0) {  // the weights: two TMA boxes of 64 K-elements x N rows
+                    mbar_arrive_tx(smem_u32(&bfull[s]), 2 * b_bytes);
+                    tma_load_2d(st + 2 * a_bytes, &bmap, smem_u32(&bfull[s]), kb * 64, P.b_row0);
+                    tma_load_2d(st + 2 * a_bytes + b_bytes, &bmap, smem_u32(&bfull[s]), kb * 64, P.b_row0 + N);
+                }
                 tr_produce_stage<EPI>(P, pt, m0, kb * 64, st, st + a_bytes, st + 2 * a_bytes, st + 2 * a_bytes + b_bytes);
                 fence_async_smem();  // generic-proxy writes -> visible to the tensor core's async proxy
                 mbar_arrive(smem_u32(&full[s]));
+            }
+        }
+        if (EPI != TR_DW && pt == 0 && !ok) {
+            // after an abort, let the weight copies still in flight land before the CTA exits
+            const uint32_t first = it > (uint32_t)P.n_stages ? it - (uint32_t)P.n_stages : 0u;
+            for (uint32_t k = first; k < it; ++k) {
+                const uint32_t s2 = k % (uint32_t)P.n_stages, ph2 = (k / (uint32_t)P.n_stages) & 1u;
+                const uint64_t t0 = globaltimer();
+                while (!mbar_try(smem_u32(&bfull[s2]), ph2) && globaltimer() - t0 < kTimeoutNs) {
+                }
             }
         }
     } else if (warp == kTrMmaWarp) {
@@ -339,6 +358,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) tr_gemm_kernel(const TrGemm P) 
                 for (int kb = kb0; kb < kb1 && ok; ++kb, ++it) {
                     const uint32_t s = it % (uint32_t)P.n_stages, round = it / (uint32_t)P.n_stages;
                     ok = wait(smem_u32(&full[s]), round & 1u);
+                    if (ok && EPI != TR_DW) ok = wait(smem_u32(&bfull[s]), round & 1u);
                     if (!ok) break;
                     tc_fence_after();
                     const uint32_t st = smem_u32(smem + (size_t)s * P.stage_bytes);
@@ -424,10 +444,10 @@ __global__ void __launch_bounds__(kTrThreads, 1) tr_gemm_kernel(const TrGemm P) 
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             const int col = c0 + 4 * j + e;
-                            z[e] = fmaf(__uint_as_float(v[4 * j + e]), inv_s, __ldg(P.bias + col));
+                            z[e] = fmaf(__uint_as_float(v[4 * j + e]), inv_s, s_c[col]);
                             const float h = tr_act(P.act, z[e], P.omega0);
-                            sa = fmaf(__ldg(P.tw + col), h, sa);
-                            if (P.mult) sb = fmaf(__ldg(P.tw + N + col), h, sb);
+                            sa = fmaf(s_c[N + col], h, sa);
+                            if (P.mult) sb = fmaf(s_c[2 * N + col], h, sb);
                         }
                         dst[j] = make_float4(z[0], z[1], z[2], z[3]);
                     }
@@ -441,8 +461,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) tr_gemm_kernel(const TrGemm P) 
                         for (int e = 0; e < 4; ++e) {
                             const int col = c0 + 4 * j + e;
                             // dt_{l-1}/dh_{l-1}: a (affine tail) or tb a + ta b (Eq. 3)
-                            const float tvec = P.mult ? fmaf(tbv, __ldg(P.tw + col), tav * __ldg(P.tw + N + col))
-                                                      : __ldg(P.tw + col);
+                            const float tvec = P.mult ? fmaf(tbv, s_c[N + col], tav * s_c[2 * N + col]) : s_c[N + col];
                             const float g = fmaf(__uint_as_float(v[4 * j + e]), inv_s, gl * tvec);
                             dd[e] = g * tr_slope(P.act, zv[e], P.omega0);
                         }
@@ -724,6 +743,7 @@ struct sand_trainer_s {
     float *params = nullptr, *grad = nullptr, *am = nullptr, *av = nullptr;
     float *scale = nullptr, *inv_scale = nullptr;
     uint16_t *wf = nullptr, *wb = nullptr;
+    CUtensorMap map_f{}, map_b{};  // TMA maps over wf and wb: rows of W fp16, boxes of 64 x W
     float *Z = nullptr, *D = nullptr, *Y = nullptr, *TA = nullptr, *TB = nullptr, *G = nullptr;
     float *dw_part = nullptr, *part = nullptr, *part_bias = nullptr, *loss_part = nullptr, *loss = nullptr;
     int *mult_of = nullptr;
@@ -739,15 +759,17 @@ constexpr int kTrLossBlocks = 304;
 size_t tr_stage_bytes(int N) { return (size_t)2 * kTrBM * 128 + (size_t)2 * N * 128; }
 
 int tr_stages(int N) {
-    const size_t misc = 1024 + 8 * (2 * kTrMaxStages + 5) + 16;
+    const size_t misc = 1024 + 8 * (3 * kTrMaxStages + 5) + 16 + (size_t)3 * N * 4;
     int s = (int)((kTrSmem - misc) / tr_stage_bytes(N));
     return s > kTrMaxStages ? kTrMaxStages : s;
 }
 
-size_t tr_smem(int N, int stages) { return 1024 + (size_t)stages * tr_stage_bytes(N) + 8 * (2 * kTrMaxStages + 5) + 16; }
+size_t tr_smem(int N, int stages) {
+    return 1024 + (size_t)stages * tr_stage_bytes(N) + 8 * (3 * kTrMaxStages + 5) + 16 + (size_t)3 * N * 4;
+}
 
 template <int EPI>
-cudaError_t tr_launch(TrGemm P, int num_sms, cudaStream_t s) {
+cudaError_t tr_launch(const CUtensorMap &bmap, TrGemm P, int num_sms, cudaStream_t s) {
     P.n_stages = tr_stages(P.N);
     P.stage_bytes = (uint32_t)tr_stage_bytes(P.N);
     const int n_tiles = P.m_tiles * P.splits;
@@ -755,7 +777,7 @@ cudaError_t tr_launch(TrGemm P, int num_sms, cudaStream_t s) {
     const size_t smem = tr_smem(P.N, P.n_stages);
     cudaError_t e = cudaFuncSetAttribute(tr_gemm_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    tr_gemm_kernel<EPI><<<grid, kTrThreads, smem, s>>>(P);
+    tr_gemm_kernel<EPI><<<grid, kTrThreads, smem, s>>>(bmap, P);
     return cudaGetLastError();
 }
 
@@ -837,6 +859,14 @@ sand_status sand_trainer_create(sand_model m, const sand_train_opts *opts, sand_
         *p.first = static_cast<char *>(T->mem) + off;
         off += (p.second + 255) / 256 * 256;
     }
+    if (!encode_u16_rows(&T->map_f, T->wf, (uint64_t)W, (uint64_t)(L - 1) * 2 * W, 64u, (uint32_t)W) ||
+        !encode_u16_rows(&T->map_b, T->wb, (uint64_t)W, (uint64_t)(L - 1) * 2 * W, 64u, (uint32_t)W)) {
+        if (prev >= 0) cudaSetDevice(prev);
+        cudaFree(T->mem);
+        delete T;
+        set_error("cannot encode the TMA tensor maps of the packed weights");
+        return SAND_ECUDA;
+    }
     std::vector<int> mult(kMaxLayers, 0);
     for (int l = 1; l < L; ++l) mult[l] = T->tail == SAND_TAIL_MULT ? 1 : 0;
     cudaError_t e = cudaMemset(T->mem, 0, total);
@@ -910,8 +940,7 @@ sand_status sand_train_step(sand_trainer T, const float *d_points, const float *
         g.omega0 = T->w0;
         g.a = Zl(l - 1);
         g.a_ld = W;
-        g.bp = T->wf + (size_t)(l - 2) * 2 * W * W;
-        g.bp_ld = W;
+        g.b_row0 = (l - 2) * 2 * W;
         g.out = Zl(l);
         g.inv_s = T->inv_scale + (l - 2);
         g.bias = P + obh + (size_t)(l - 2) * W;
@@ -926,7 +955,7 @@ sand_status sand_train_step(sand_trainer T, const float *d_points, const float *
         g.m_tiles = row_tiles;
         g.splits = 1;
         g.kb_per_split = W / 64;
-        SAND_CUDA(tr_launch<TR_FWD>(g, T->num_sms, s), "forward GEMM");
+        SAND_CUDA(tr_launch<TR_FWD>(T->map_f, g, T->num_sms, s), "forward GEMM");
     }
     // loss, dL/dt (as the integers G'), delta'_L
     tr_loss_kernel<<<T->loss_blocks, 256, 0, s>>>(T->Y, d_targets, n, B, cap, L, T->G, T->loss_part);
@@ -953,8 +982,7 @@ sand_status sand_train_step(sand_trainer T, const float *d_points, const float *
         g.omega0 = T->w0;
         g.a = Dl(l);
         g.a_ld = W;
-        g.bp = T->wb + (size_t)(l - 2) * 2 * W * W;
-        g.bp_ld = W;
+        g.b_row0 = (l - 2) * 2 * W;
         g.out = Dl(l - 1);
         g.inv_s = T->inv_scale + (l - 2);
         g.tw = P + otw + (size_t)(l - 2) * 2 * W;
@@ -967,7 +995,7 @@ sand_status sand_train_step(sand_trainer T, const float *d_points, const float *
         g.m_tiles = row_tiles;
         g.splits = 1;
         g.kb_per_split = W / 64;
-        SAND_CUDA(tr_launch<TR_BWD>(g, T->num_sms, s), "backward GEMM");
+        SAND_CUDA(tr_launch<TR_BWD>(T->map_b, g, T->num_sms, s), "backward GEMM");
         TrGemm w{};
         w.M = W;
         w.N = W;
@@ -983,7 +1011,7 @@ sand_status sand_train_step(sand_trainer T, const float *d_points, const float *
         w.status = T->status;
         w.m_tiles = m_tiles;
         w.splits = splits;
-        SAND_CUDA(tr_launch<TR_DW>(w, T->num_sms, s), "weight-gradient GEMM");
+        SAND_CUDA(tr_launch<TR_DW>(T->map_f, w, T->num_sms, s), "weight-gradient GEMM");  // (map unused)
         if (splits < T->S_dw)  // unused split slots must read as zero
             SAND_CUDA(cudaMemsetAsync(w.out + (size_t)splits * W * W, 0, (size_t)(T->S_dw - splits) * W * W * 4, s),
                       "partials reset");
