@@ -55,14 +55,15 @@ struct TrGemm {
     int kb_per_split;     // 64-element K-blocks per split
     int act;
     float omega0;
-    // A operand: FWD act(a[row][k]); BWD a[row][k]; DW a[k][row]   (ld = a_ld)
+    // A operand: FWD act(a[row][k]); BWD a[row][k]   (ld = a_ld); DW: rows a_row0 + m (hi) and
+    // a_row0 + W + m (lo) of the kernel's A tensor map (delta'^T split into fp16, k contiguous)
     const float *a;
     int a_ld;
-    // B operand: FWD / BWD packed fp16 rows [hi rows; lo rows] of K elements, loaded by TMA through
-    // the kernel's tensor map from row b_row0 (hi) and b_row0 + N (lo) on; DW act(b[k][n])
+    int a_row0;
+    // B operand by TMA through the kernel's B tensor map, rows b_row0 + n (hi) and b_row0 + N + n
+    // (lo): FWD / BWD the packed weights; DW act(z)^T split into fp16 (k contiguous)
     int b_row0;
-    const float *b;
-    int b_ld;
+    int box_rows;  // DW: rows per TMA box of either map (min(128, W))
     int n_stages;
     uint32_t stage_bytes;
     // epilogue
@@ -138,16 +139,17 @@ __device__ __forceinline__ bool tr_wait_warp(uint32_t bar, uint32_t parity, vola
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
-// One stage of operands (64 K-elements of a 128-row A tile and an N-row B tile) from global memory
-// into shared memory, split into fp16 hi and lo parts, by the kTrProducers producer threads (FWD /
-// BWD: the A tile only; the packed weights come by TMA).
+// The A tile of one FWD / BWD stage (64 K-elements of 128 rows) from global memory into shared
+// memory, split into fp16 hi and lo parts, by the kTrProducers producer threads (the packed
+// weights come by TMA).
 // Every global load of a group is issued before any of its values is used, so a stage costs a
 // few memory latencies rather than one per chunk.
 template <int EPI>
 __device__ __forceinline__ void tr_produce_stage(const TrGemm &P, int pt, int m0, int k0, uint32_t ahi, uint32_t alo,
                                                  uint32_t bhi, uint32_t blo) {
-    const int N = P.N;
-    if (EPI != TR_DW) {
+    (void)bhi;
+    (void)blo;
+    {
         // A[r][kk] = (act of) a[m0 + r][k0 + kk]: chunk it = (row it / 8, 8 K-elements it % 8), 32
         // contiguous bytes; eight consecutive threads read one row's 256 bytes
         constexpr int NA = kTrBM * 8 / kTrProducers;
@@ -174,65 +176,20 @@ __device__ __forceinline__ void tr_produce_stage(const TrGemm &P, int pt, int m0
             st_shared_v4(ahi + tr_swz(it >> 3, it & 7), hi);
             st_shared_v4(alo + tr_swz(it >> 3, it & 7), lo);
         }
-    } else {
-        // Both operands are [k][row] in memory (rows contiguous).  A quad is four consecutive rows
-        // of one chunk: eight float4 loads along the rows, one per K-element, give four chunks.
-        // Consecutive threads take consecutive quads of the same chunk column.
-        // A[r][kk] = delta'[k0 + kk][m0 + r]: 32 quads per chunk column, 256 in all
-        constexpr int NQ = 2;  // quads per thread per group
-        for (int g0 = 0; g0 < kTrBM * 2 + N * 2; g0 += NQ * kTrProducers) {
-            const bool is_a = g0 < kTrBM * 2;  // groups never straddle A and B (both are multiples)
-            float4 vq[NQ][8];
-#pragma unroll
-            for (int j = 0; j < NQ; ++j) {
-                const int q = g0 + pt + j * kTrProducers - (is_a ? 0 : kTrBM * 2);
-                const int nq = is_a ? 32 : (N >> 2);
-                const int q4 = q % nq, c = q / nq;
-                const int row0 = (is_a ? m0 : 0) + 4 * q4;
-                const bool in = q < (is_a ? kTrBM * 2 : N * 2) && (!is_a || row0 + 4 <= P.M);
-                const float *base = is_a ? P.a : P.b;
-                const int ld = is_a ? P.a_ld : P.b_ld;
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int kk = k0 + 8 * c + e;
-                    vq[j][e] = (in && kk < P.K) ? __ldg(reinterpret_cast<const float4 *>(base + (size_t)kk * ld + row0))
-                                                : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < NQ; ++j) {
-                const int q = g0 + pt + j * kTrProducers - (is_a ? 0 : kTrBM * 2);
-                if (q >= (is_a ? kTrBM * 2 : N * 2)) continue;
-                const int nq = is_a ? 32 : (N >> 2);
-                const int q4 = q % nq, c = q / nq;
-                const uint32_t dhi = is_a ? ahi : bhi, dlo = is_a ? alo : blo;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    float v[8];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const float x = i == 0 ? vq[j][e].x : i == 1 ? vq[j][e].y : i == 2 ? vq[j][e].z : vq[j][e].w;
-                        v[e] = is_a ? x : tr_act(P.act, x, P.omega0);  // B = act(z_{l-1})
-                    }
-                    uint4 hi, lo;
-                    tr_split8(v, hi, lo);
-                    st_shared_v4(dhi + tr_swz(4 * q4 + i, c), hi);
-                    st_shared_v4(dlo + tr_swz(4 * q4 + i, c), lo);
-                }
-            }
-        }
     }
 }
 
 // Persistent GEMM: CTA b takes tiles b, b + grid, ...; tile t is rows 128 (t % m_tiles) .. + 127
 // and K-blocks of split t / m_tiles.  Two accumulators in TMEM let the epilogue of one tile run
-// while the MMAs of the next one do.  FWD / BWD: the packed weights of a stage (hi and lo) come
-// by two TMA copies (bmap, 128-byte swizzle: the layout tr_swz writes) on their own barrier.
+// while the MMAs of the next one do.  The B operand of a stage (hi and lo) comes by TMA (bmap,
+// 128-byte swizzle: the layout tr_swz writes) on its own barrier; DW's A operand too (amap), so
+// its producer is one thread of warp 0 and its stages hold no generic-proxy writes.
 //   warps 0..3  producers (operands into the shared-memory stage ring)
 //   warp 4      TMEM owner, MMA issuer (one thread)
 //   warps 5..8  epilogue: thread (quadrant warp & 3, lane i) owns tile row 32 (warp & 3) + i
 template <int EPI>
-__global__ void __launch_bounds__(kTrThreads, 1) tr_gemm_kernel(const __grid_constant__ CUtensorMap bmap, const TrGemm P) {
+__global__ void __launch_bounds__(kTrThreads, 1) tr_gemm_kernel(const __grid_constant__ CUtensorMap amap,
+                                                                const __grid_constant__ CUtensorMap bmap, const TrGemm P) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)P.n_stages * P.stage_bytes);
@@ -295,7 +252,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) tr_gemm_kernel(const __grid_con
         const int pt = threadIdx.x;
         uint32_t it = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        for (int t = blockIdx.x; t < n_tiles && ok && (EPI != TR_DW || warp == 0); t += gridDim.x) {
             int m0, kb0, kb1;
             tile_kb(t, m0, kb0, kb1);
             for (int kb = kb0; kb < kb1 && ok; ++kb, ++it) {
@@ -305,7 +262,22 @@ __global__ void __launch_bounds__(kTrThreads, 1) tr_gemm_kernel(const __grid_con
                     if (!ok) break;
                 }
                 const uint32_t st = smem_u32(smem + (size_t)s * P.stage_bytes);
-                if (EPI != TR_DW && pt == 0) {  // the weights: two TMA boxes of 64 K-elements x N rows
+                if (EPI == TR_DW) {  // both operands: boxes of 64 K-elements x box_rows rows
+                    if (pt == 0) {
+                        const int ar = min(kTrBM, P.M), br = P.box_rows;
+                        mbar_arrive_tx(smem_u32(&bfull[s]), (uint32_t)(2 * ar + 2 * N) * 128u);
+                        for (int part = 0; part < 2; ++part) {
+                            for (int r = 0; r < ar; r += br)
+                                tma_load_2d(st + part * a_bytes + r * 128, &amap, smem_u32(&bfull[s]), kb * 64,
+                                            P.a_row0 + part * P.M + m0 + r);
+                            for (int r = 0; r < N; r += br)
+                                tma_load_2d(st + 2 * a_bytes + part * b_bytes + r * 128, &bmap, smem_u32(&bfull[s]),
+                                            kb * 64, P.b_row0 + part * N + r);
+                        }
+                    }
+                    continue;
+                }
+                if (pt == 0) {  // the weights: two TMA boxes of 64 K-elements x N rows
                     mbar_arrive_tx(smem_u32(&bfull[s]), 2 * b_bytes);
                     tma_load_2d(st + 2 * a_bytes, &bmap, smem_u32(&bfull[s]), kb * 64, P.b_row0);
                     tma_load_2d(st + 2 * a_bytes + b_bytes, &bmap, smem_u32(&bfull[s]), kb * 64, P.b_row0 + N);
@@ -315,7 +287,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) tr_gemm_kernel(const __grid_con
                 mbar_arrive(smem_u32(&full[s]));
             }
         }
-        if (EPI != TR_DW && pt == 0 && !ok) {
+        if (pt == 0 && !ok) {
             // after an abort, let the weight copies still in flight land before the CTA exits
             const uint32_t first = it > (uint32_t)P.n_stages ? it - (uint32_t)P.n_stages : 0u;
             for (uint32_t k = first; k < it; ++k) {
@@ -357,8 +329,8 @@ __global__ void __launch_bounds__(kTrThreads, 1) tr_gemm_kernel(const __grid_con
                 uint32_t acc = 0;
                 for (int kb = kb0; kb < kb1 && ok; ++kb, ++it) {
                     const uint32_t s = it % (uint32_t)P.n_stages, round = it / (uint32_t)P.n_stages;
-                    ok = wait(smem_u32(&full[s]), round & 1u);
-                    if (ok && EPI != TR_DW) ok = wait(smem_u32(&bfull[s]), round & 1u);
+                    if (EPI != TR_DW) ok = wait(smem_u32(&full[s]), round & 1u);
+                    if (ok) ok = wait(smem_u32(&bfull[s]), round & 1u);
                     if (!ok) break;
                     tc_fence_after();
                     const uint32_t st = smem_u32(smem + (size_t)s * P.stage_bytes);
@@ -562,6 +534,38 @@ __global__ void tr_fwd1_kernel(const float *pts, int64_t n, int64_t B, int W, in
     }
 }
 
+// The weight-gradient operands, transposed and split: out[z][0][n][k] + out[z][1][n][k] = f(X[z][k][n])
+// (hi = fp16 of the value, lo = fp16 of the rest, as the GEMM producers split) for n < W, k < B, with
+// f the activation (act >= 0) or the identity (act < 0): rows of `cap` fp16, k contiguous, the
+// K-major layout the weight-gradient GEMM loads by TMA.  One block per 64 x 64 tile, through shared
+// memory so that both the reads (along n) and the writes (along k) are coalesced.
+__global__ void __launch_bounds__(256) tr_tsplit_kernel(const float *X, int W, int act, float w0, uint16_t *out,
+                                                       int64_t cap) {
+    __shared__ float tile[64][65];
+    const int64_t k0 = (int64_t)blockIdx.x * 64;
+    const int n0 = blockIdx.y * 64;
+    const float *Xz = X + (size_t)blockIdx.z * cap * W;
+    uint16_t *hi = out + (size_t)blockIdx.z * 2 * W * cap, *lo = hi + (size_t)W * cap;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int idx = threadIdx.x + 256 * i, r = idx >> 6, c = idx & 63;
+        const float v = Xz[(k0 + r) * W + n0 + c];
+        tile[r][c] = act >= 0 ? tr_act(act, v, w0) : v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int idx = threadIdx.x + 256 * i, nl = idx >> 5, kp = idx & 31;
+        const float a = tile[2 * kp][nl], b = tile[2 * kp + 1][nl];
+        const __half2 hp = __floats2half2_rn(a, b);
+        const float2 hf = __half22float2(hp);
+        const __half2 lp = __floats2half2_rn(a - hf.x, b - hf.y);
+        const size_t at = (size_t)(n0 + nl) * cap + k0 + 2 * kp;
+        *reinterpret_cast<__half2 *>(hi + at) = hp;
+        *reinterpret_cast<__half2 *>(lo + at) = lp;
+    }
+}
+
 // Per row: G'_k = sum_{i >= k} sign(y_i - y_gt) (0 for padding rows); per block: sum of |y_i - y_gt|.
 __global__ void tr_loss_kernel(const float *Y, const float *gt, int64_t n, int64_t B, int64_t ld, int L, float *G,
                                float *loss_part) {
@@ -695,6 +699,15 @@ __global__ void tr_finalize_kernel(const float *part, const float *part_bias, co
         }
         float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         int s = 0;
+        for (; s + 16 <= count; s += 16) {  // sixteen loads in flight, added in the order of the loop below
+            float v[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) v[u] = base[(size_t)(s + u) * stride];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] += v[u];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] += v[8 + u];
+        }
         for (; s + 8 <= count; s += 8) {
 #pragma unroll
             for (int u = 0; u < 8; ++u) acc[u] += base[(size_t)(s + u) * stride];
@@ -744,6 +757,10 @@ struct sand_trainer_s {
     float *scale = nullptr, *inv_scale = nullptr;
     uint16_t *wf = nullptr, *wb = nullptr;
     CUtensorMap map_f{}, map_b{};  // TMA maps over wf and wb: rows of W fp16, boxes of 64 x W
+    // weight-gradient operands [L-1][hi, lo][W][cap] fp16: delta'_l^T (l = 2..L) and act(z_l)^T
+    // (l = 1..L-1), with their TMA maps (boxes of 64 x min(128, W))
+    uint16_t *dt = nullptr, *ht = nullptr;
+    CUtensorMap map_dt{}, map_ht{};
     float *Z = nullptr, *D = nullptr, *Y = nullptr, *TA = nullptr, *TB = nullptr, *G = nullptr;
     float *dw_part = nullptr, *part = nullptr, *part_bias = nullptr, *loss_part = nullptr, *loss = nullptr;
     int *mult_of = nullptr;
@@ -769,7 +786,7 @@ size_t tr_smem(int N, int stages) {
 }
 
 template <int EPI>
-cudaError_t tr_launch(const CUtensorMap &bmap, TrGemm P, int num_sms, cudaStream_t s) {
+cudaError_t tr_launch(const CUtensorMap &amap, const CUtensorMap &bmap, TrGemm P, int num_sms, cudaStream_t s) {
     P.n_stages = tr_stages(P.N);
     P.stage_bytes = (uint32_t)tr_stage_bytes(P.N);
     const int n_tiles = P.m_tiles * P.splits;
@@ -777,7 +794,7 @@ cudaError_t tr_launch(const CUtensorMap &bmap, TrGemm P, int num_sms, cudaStream
     const size_t smem = tr_smem(P.N, P.n_stages);
     cudaError_t e = cudaFuncSetAttribute(tr_gemm_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    tr_gemm_kernel<EPI><<<grid, kTrThreads, smem, s>>>(bmap, P);
+    tr_gemm_kernel<EPI><<<grid, kTrThreads, smem, s>>>(amap, bmap, P);
     return cudaGetLastError();
 }
 
@@ -839,6 +856,7 @@ sand_status sand_trainer_create(sand_model m, const sand_train_opts *opts, sand_
         {(void **)&T->params, T->np * 4}, {(void **)&T->grad, T->np * 4}, {(void **)&T->am, T->np * 4},
         {(void **)&T->av, T->np * 4}, {(void **)&T->scale, 4 * kMaxLayers}, {(void **)&T->inv_scale, 4 * kMaxLayers},
         {(void **)&T->wf, (size_t)(L - 1) * 2 * W * W * 2}, {(void **)&T->wb, (size_t)(L - 1) * 2 * W * W * 2},
+        {(void **)&T->dt, (size_t)(L - 1) * 2 * W * B * 2}, {(void **)&T->ht, (size_t)(L - 1) * 2 * W * B * 2},
         {(void **)&T->Z, (size_t)L * B * W * 4}, {(void **)&T->D, (size_t)L * B * W * 4},
         {(void **)&T->Y, (size_t)L * B * 4}, {(void **)&T->TA, (size_t)L * B * 4}, {(void **)&T->TB, (size_t)L * B * 4},
         {(void **)&T->G, (size_t)L * B * 4}, {(void **)&T->dw_part, (size_t)(L - 1) * T->S_dw * W * W * 4},
@@ -859,8 +877,11 @@ sand_status sand_trainer_create(sand_model m, const sand_train_opts *opts, sand_
         *p.first = static_cast<char *>(T->mem) + off;
         off += (p.second + 255) / 256 * 256;
     }
+    const uint32_t box_r = W < kTrBM ? (uint32_t)W : (uint32_t)kTrBM;
     if (!encode_u16_rows(&T->map_f, T->wf, (uint64_t)W, (uint64_t)(L - 1) * 2 * W, 64u, (uint32_t)W) ||
-        !encode_u16_rows(&T->map_b, T->wb, (uint64_t)W, (uint64_t)(L - 1) * 2 * W, 64u, (uint32_t)W)) {
+        !encode_u16_rows(&T->map_b, T->wb, (uint64_t)W, (uint64_t)(L - 1) * 2 * W, 64u, (uint32_t)W) ||
+        !encode_u16_rows(&T->map_dt, T->dt, (uint64_t)B, (uint64_t)(L - 1) * 2 * W, 64u, box_r) ||
+        !encode_u16_rows(&T->map_ht, T->ht, (uint64_t)B, (uint64_t)(L - 1) * 2 * W, 64u, box_r)) {
         if (prev >= 0) cudaSetDevice(prev);
         cudaFree(T->mem);
         delete T;
@@ -955,7 +976,7 @@ sand_status sand_train_step(sand_trainer T, const float *d_points, const float *
         g.m_tiles = row_tiles;
         g.splits = 1;
         g.kb_per_split = W / 64;
-        SAND_CUDA(tr_launch<TR_FWD>(T->map_f, g, T->num_sms, s), "forward GEMM");
+        SAND_CUDA(tr_launch<TR_FWD>(T->map_f, T->map_f, g, T->num_sms, s), "forward GEMM");
     }
     // loss, dL/dt (as the integers G'), delta'_L
     tr_loss_kernel<<<T->loss_blocks, 256, 0, s>>>(T->Y, d_targets, n, B, cap, L, T->G, T->loss_part);
@@ -968,6 +989,13 @@ sand_status sand_train_step(sand_trainer T, const float *d_points, const float *
                                                         W, T->act, T->w0, Dl(L));
         SAND_CUDA(cudaGetLastError(), "top-layer delta kernel");
     }
+    // the weight-gradient operands known so far: act(z_l)^T for l = 1..L-1 and delta'_L^T
+    tr_tsplit_kernel<<<dim3((unsigned)(B / 64), (unsigned)(W / 64), (unsigned)(L - 1)), 256, 0, s>>>(
+        Zl(1), W, T->act, T->w0, T->ht, cap);
+    SAND_CUDA(cudaGetLastError(), "activation transpose kernel");
+    tr_tsplit_kernel<<<dim3((unsigned)(B / 64), (unsigned)(W / 64), 1), 256, 0, s>>>(
+        Dl(L), W, -1, 0.f, T->dt + (size_t)(L - 2) * 2 * W * cap, cap);
+    SAND_CUDA(cudaGetLastError(), "delta transpose kernel");
     // backward: delta'_{l-1} from delta'_l, and the weight-gradient partials of layer l
     const int m_tiles = (W + kTrBM - 1) / kTrBM;
     const int kb_all = (int)(B / 64);
@@ -995,7 +1023,13 @@ sand_status sand_train_step(sand_trainer T, const float *d_points, const float *
         g.m_tiles = row_tiles;
         g.splits = 1;
         g.kb_per_split = W / 64;
-        SAND_CUDA(tr_launch<TR_BWD>(T->map_b, g, T->num_sms, s), "backward GEMM");
+        SAND_CUDA(tr_launch<TR_BWD>(T->map_b, T->map_b, g, T->num_sms, s), "backward GEMM");
+        // delta'_{l-1}, transposed and split for the weight gradient of layer l - 1
+        if (l - 1 >= 2) {
+            tr_tsplit_kernel<<<dim3((unsigned)(B / 64), (unsigned)(W / 64), 1), 256, 0, s>>>(
+                Dl(l - 1), W, -1, 0.f, T->dt + (size_t)(l - 3) * 2 * W * cap, cap);
+            SAND_CUDA(cudaGetLastError(), "delta transpose kernel");
+        }
         TrGemm w{};
         w.M = W;
         w.N = W;
@@ -1003,15 +1037,14 @@ sand_status sand_train_step(sand_trainer T, const float *d_points, const float *
         w.kb_per_split = kb_per;
         w.act = T->act;
         w.omega0 = T->w0;
-        w.a = Dl(l);
-        w.a_ld = W;
-        w.b = Zl(l - 1);
-        w.b_ld = W;
+        w.a_row0 = (l - 2) * 2 * W;
+        w.b_row0 = (l - 2) * 2 * W;
+        w.box_rows = (int)(W < kTrBM ? W : kTrBM);
         w.out = T->dw_part + (size_t)(l - 2) * T->S_dw * W * W;
         w.status = T->status;
         w.m_tiles = m_tiles;
         w.splits = splits;
-        SAND_CUDA(tr_launch<TR_DW>(T->map_f, w, T->num_sms, s), "weight-gradient GEMM");  // (map unused)
+        SAND_CUDA(tr_launch<TR_DW>(T->map_dt, T->map_ht, w, T->num_sms, s), "weight-gradient GEMM");
         if (splits < T->S_dw)  // unused split slots must read as zero
             SAND_CUDA(cudaMemsetAsync(w.out + (size_t)splits * W * W, 0, (size_t)(T->S_dw - splits) * W * W * 4, s),
                       "partials reset");
@@ -1023,8 +1056,10 @@ sand_status sand_train_step(sand_trainer T, const float *d_points, const float *
                                                                          cap, W, T->act, T->w0, T->mult_of, rows_per,
                                                                          T->part, T->part_bias);
         SAND_CUDA(cudaGetLastError(), "column-sum kernel");
-        tr_finalize_kernel<<<2 * T->num_sms, 256, 0, s>>>(T->part, T->part_bias, T->dw_part, T->S, T->S_dw, W, L,
-                                                          (float)(1.0 / (double)n), T->grad);
+        // one element per thread: each sums its S (or S_dw) partials with sixteen loads in flight
+        const unsigned fin_blocks = (unsigned)((T->np + 255) / 256);
+        tr_finalize_kernel<<<fin_blocks, 256, 0, s>>>(T->part, T->part_bias, T->dw_part, T->S, T->S_dw, W, L,
+                                                      (float)(1.0 / (double)n), T->grad);
         SAND_CUDA(cudaGetLastError(), "gradient kernel");
         tr_loss_final_kernel<<<1, 32, 0, s>>>(T->loss_part, T->loss_blocks, (float)(1.0 / (double)n),
                                               d_loss ? d_loss : T->loss);
