@@ -536,7 +536,10 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
     uint64_t *x_empty = x_full + 1; // ... and read by slice 0 (128 arrivals)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + kNumBars);
     volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
-    volatile int *skip = reinterpret_cast<volatile int *>(tmem_slot + 2);  // dynamic exit: the tile is done
+    // dynamic exit: tiles whose rows have all stopped, as counts: requested by the epilogue,
+    // taken up by the MMA thread
+    volatile int *skip_req = reinterpret_cast<volatile int *>(tmem_slot + 2);
+    volatile int *skip_done = reinterpret_cast<volatile int *>(tmem_slot + 3);
     float *tailx = reinterpret_cast<float *>(tmem_slot + 4);  // [kSlices - 1][2 values][128 rows]
     float4 *rowbuf = reinterpret_cast<float4 *>((reinterpret_cast<uintptr_t>(tailx + (kSlices - 1) * 256) + 15) &
                                                 ~uintptr_t(15));  // [2][kEpiThreads]
@@ -571,7 +574,8 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
         mbar_init(smem_u32(x_full), (kSlices - 1) * 128);
         mbar_init(smem_u32(x_empty), 128);
         *abort = 0;
-        *skip = 0;
+        *skip_req = 0;
+        *skip_done = 0;
         for (int k = 0; k < 16; ++k) s_bin[k] = hdr->bin_start[k];
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -659,6 +663,7 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
             bool ok = true, any_layer = false;
             bool drained_credit = false;  // dynamic exit: the last drained accumulator was not overwritten
             const bool dyn = EXT && P.dyn_r > 0.f;
+            int skips_seen = 0;
             for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
                 const int Dt = tile_depth(t);
                 bool tile_skip = false;
@@ -703,8 +708,8 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                                     e_seen = e;
                                     if (!ok) break;
                                     tc_fence_after();
-                                    if (dyn && e == 0 && *skip) {  // every row of the tile has stopped
-                                        *skip = 0;
+                                    if (dyn && e == 0 && *skip_req > skips_seen) {  // every row of the tile has stopped
+                                        *skip_done = ++skips_seen;
                                         tile_skip = true;
                                         break;
                                     }
@@ -948,7 +953,36 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
         };
         int buf = 0;
         prefetch_row(blockIdx.x, 0);
+        // Dynamic exit: a skipped tile hands the MMA thread its a_ready[0] phase with no MMA after it,
+        // so before a tile sends anything the MMA thread must have taken up every earlier skip (else
+        // a second phase of a_ready[0] could complete before it has seen the first, and its parity
+        // wait would miss both).  Bounded like every wait.
+        int my_skips = 0;
+        auto skips_taken = [&]() -> bool {
+            const uint64_t t0 = globaltimer();
+            bool good = true;
+            while (*skip_done < my_skips) {
+                if (globaltimer() - t0 > P.wait_ns) {
+                    good = false;
+                    break;
+                }
+            }
+            good = __all_sync(0xffffffffu, good);
+            if (!good) {
+                *abort = 1;
+                atomicOr(&hdr->flags, (uint32_t)SAND_FLAG_TIMEOUT);
+                atomicExch(&hdr->timeout_where, 10u);
+            }
+            return good;
+        };
         for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, buf ^= 1) {
+            if (EXT && P.dyn_r > 0.f && my_skips > 0) {
+                // every epilogue warp takes the same decision (named barriers follow in the tile)
+                if (named_count(1, kEpiThreads, !skips_taken()) > 0) {
+                    ok = false;
+                    break;
+                }
+            }
             const int Dt = tile_depth(t);
             const TcRow cur = take_row(t, buf);
             prefetch_row(t + gridDim.x, buf ^ 1);  // the next tile's rows, in flight during this tile
@@ -985,7 +1019,8 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                     if (n_alive > 0) {
                         for (int kb = 0; kb < KB; ++kb) signal(&a_ready[kb], true);
                     } else {
-                        if (threadIdx.x == 64) *skip = 1;
+                        ++my_skips;
+                        if (threadIdx.x == 64) *skip_req = my_skips;
                         signal(&a_ready[0], true);
                         l_end = 0;
                     }
@@ -1102,7 +1137,8 @@ tmlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const TcParams P, const
                     if (n_alive > 0) {
                         for (int kb = 0; kb < KB; ++kb) signal(&a_ready[kb], true);
                     } else {
-                        if (threadIdx.x == 64) *skip = 1;
+                        ++my_skips;
+                        if (threadIdx.x == 64) *skip_req = my_skips;
                         signal(&a_ready[0], true);
                         break;
                     }

@@ -82,6 +82,31 @@ def test_dynamic_sphere_tiles_skip():
     m.free()
 
 
+@pytest.mark.parametrize("kind", ["siren", "sphere"])
+def test_dynamic_every_tile_stops_at_layer_1(kind):
+    """r above every |t_1|: every row stops at layer 1, so every tile of every CTA is skipped one
+    after the other, with no MMA between the skips (layer 1 of the SIREN's raw coordinates runs on
+    the CUDA cores; the sphere's multiplicative tails keep it as one MMA).  The kernel must hand
+    each skip to the MMA thread in turn: all exit layers 1, values t_1, no timeout."""
+    if kind == "siren":
+        model = synth.siren_tmlp(8, 256, seed=1)
+    else:
+        model = synth.relu_sphere_tmlp(0.6, width=64)
+    m = load(model)
+    pts = synth.uniform_points(300001, seed=47)
+    _, _, ys = oracle.dynamic_exit(model, pts[:20000], 1e9)
+    r = float(1.5 * np.abs(ys[:, 0]).max() + 0.1)
+    y, el = m.query_dynamic(torch.from_numpy(pts).cuda(), r=r)
+    st = m.stats()  # the model's own workspace; raises SandError (ETIMEOUT) if a wait ran out
+    assert not (st["flags"] & 2), "a device-side wait timed out"
+    assert (el.cpu().numpy() == 1).all()
+    idx = synth.sample_indices(len(pts), 20000, seed=3)
+    y_ref, d_ref, _ = oracle.dynamic_exit(model, pts[idx], r)
+    assert (d_ref == 1).all()
+    assert np.abs(y.double().cpu().numpy()[idx] - y_ref).max() <= TOL
+    m.free()
+
+
 def test_dynamic_errors():
     from paper_2604_25936_gb300 import SandError
     model = synth.siren_tmlp(4, 64, seed=0)
