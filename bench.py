@@ -336,7 +336,8 @@ def _open_loop(sand, srv, pool, lam: float, seconds: float, g):
 def serve_bench(sand, models, precision, pool, run_s: float, sweep_s: float, mem_budget: int = 16 << 30):
     """Continuous batching over the three resident models: a closed burst of the pool estimates
     the saturation rate; open-loop Poisson runs of sweep_s seconds at 0.25 .. 1.5 of that
-    estimate find the saturation throughput (the largest completed queries/s); then open-loop
+    estimate, and beyond while the server keeps up, find the saturation throughput (the largest
+    completed queries/s); then open-loop
     runs of run_s seconds at 0.5x and 0.8x of saturation report p50 / p99 request latency
     (submit to result) and aggregate queries/s."""
     import torch
@@ -364,13 +365,22 @@ def serve_bench(sand, models, precision, pool, run_s: float, sweep_s: float, mem
     out["burst_qps"] = burst_qps
     g = np.random.Generator(np.random.PCG64(99))
     sweep = []
-    for frac in (0.25, 0.5, 0.75, 1.0, 1.25, 1.5):
+    # 0.25 .. 1.5 of the burst estimate, then on in steps of 0.5 (up to 4) while the server still
+    # keeps up (completes at least 95 % of the offered rate): a short burst can under-read the
+    # saturation rate, and the load levels below are fractions of the largest completed rate
+    fracs = [0.25, 0.5, 0.75, 1.0, 1.25, 1.5]
+    i = 0
+    while i < len(fracs):
+        frac = fracs[i]
         srv = server()
         st = _open_loop(sand, srv, pool, frac * burst_qps / mean_pts, sweep_s, g)
         srv.close()
         sweep.append({"offered_fraction_of_burst": frac, "offered_queries_per_s": frac * burst_qps,
                       "queries_per_s": st["queries_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
                       "requests": st["requests"], "max_outstanding": st["max_outstanding"]})
+        if i == len(fracs) - 1 and st["queries_per_s"] >= 0.95 * frac * burst_qps and frac < 4.0:
+            fracs.append(frac + 0.5)
+        i += 1
     sat_qps = max(e["queries_per_s"] for e in sweep)
     out["lambda_sweep"] = sweep
     out["saturation_qps"] = sat_qps
