@@ -181,9 +181,10 @@ sand_status sand_query_sdf_grad(sand_model m, const float *d_points, int64_t n, 
 
 /* End-to-end query from HOST memory: copies h_points to the device, runs the
  * query, copies the SDF back to h_out.  From 2^20 points on the work goes in up
- * to four chunks as a pipeline: chunk k (the blocks k, k + 4, k + 8, ... of 2^18
- * consecutive points, so that every chunk samples the whole input) is copied up
- * on a copy stream of the model's own, its query runs on `stream` once it has
+ * to four chunks as a pipeline.  The points are cut into blocks of 2^18; of every
+ * ten blocks chunk 0 takes one, chunks 1 and 2 four each and chunk 3 one (small
+ * first and last chunks, each chunk sampling the whole input).  A chunk is copied
+ * up on a copy stream of the model's own, its query runs on `stream` once it has
  * arrived, and its values are copied down on a second copy stream once it is
  * done, so the copies of one chunk overlap the queries of the others.  Each chunk is a query of its own points, which leaves every point's
  * result unchanged (results do not depend on the batch); sand_read_stats then

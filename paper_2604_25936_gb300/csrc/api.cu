@@ -713,16 +713,22 @@ sand_status sand_query_sdf_host(sand_model m, const float *h_points, int64_t n, 
     float *d_out = m->d_stage + (size_t)n * 3;
     // A pipeline of chunks: chunk k's points go up on copy_in, its query runs on the caller's
     // stream once they are there, and its values come down on copy_out once it is done, so
-    // the copies of one chunk overlap the queries of the others.  Chunk k is made of the
-    // blocks k, k + n_chunks, k + 2 n_chunks, ... of kHostBlock consecutive points, packed
-    // together on the device: spread over the whole input, every chunk gets about the same
-    // mix of exit layers (a contiguous slab of a spatially ordered input may be all far field
-    // or all surface, which leaves one kind of warp of the T-MLP kernel idle).  Each chunk is
-    // a query of its own points (a point's result does not depend on the other points).
+    // the copies of one chunk overlap the queries of the others.  The input is cut into blocks
+    // of kHostBlock consecutive points; of every ten blocks, chunk 0 takes the first, chunk 1
+    // the next four, chunk 2 four more and chunk 3 the last, packed together on the device.
+    // The first chunk is small because nothing overlaps its upload, the last because nothing
+    // overlaps its download; spread over the whole input, every chunk gets about the same mix
+    // of exit layers (a contiguous slab of a spatially ordered input may be all far field or
+    // all surface, which leaves one kind of warp of the T-MLP kernel idle).  Each chunk is a
+    // query of its own points (a point's result does not depend on the other points).
     constexpr int kHostChunks = 4;
     constexpr int64_t kHostBlock = (int64_t)1 << 18;
     const int64_t n_blocks = (n + kHostBlock - 1) / kHostBlock;
-    const int n_chunks = n < ((int64_t)1 << 20) ? 1 : (int)(n_blocks < kHostChunks ? n_blocks : kHostChunks);
+    auto chunk_of = [](int64_t b) {
+        const int r = (int)(b % 10);
+        return r == 0 ? 0 : r <= 4 ? 1 : r <= 8 ? 2 : 3;
+    };
+    const int n_chunks = n < ((int64_t)1 << 20) ? 1 : kHostChunks;
     if (n_chunks <= 1) {
         SAND_CUDA(cudaMemcpyAsync(d_pts, h_points, (size_t)n * 12, cudaMemcpyHostToDevice, s), "H2D points");
         st = run_query(m, d_pts, n, d_out, nullptr, &o, stream);
@@ -753,12 +759,14 @@ sand_status sand_query_sdf_host(sand_model m, const float *h_points, int64_t n, 
     int64_t base = 0;  // first device row of chunk k
     for (int k = 0; k < n_chunks && ce == cudaSuccess && st == SAND_OK; ++k) {
         int64_t cnt = 0;
-        for (int64_t b = k; b < n_blocks && ce == cudaSuccess; b += n_chunks) {
+        for (int64_t b = 0; b < n_blocks && ce == cudaSuccess; ++b) {
+            if (chunk_of(b) != k) continue;
             const int64_t off = b * kHostBlock, len = n - off < kHostBlock ? n - off : kHostBlock;
             ce = cudaMemcpyAsync(d_pts + 3 * (base + cnt), h_points + 3 * off, (size_t)len * 12, cudaMemcpyHostToDevice,
                                  m->copy_in);
             cnt += len;
         }
+        if (cnt == 0) continue;  // (fewer than ten blocks: the later chunks may be empty)
         if (ce == cudaSuccess) ce = cudaEventRecord(ev[2 * k], m->copy_in);
         if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s, ev[2 * k], 0);
         if (ce != cudaSuccess) break;
@@ -767,7 +775,8 @@ sand_status sand_query_sdf_host(sand_model m, const float *h_points, int64_t n, 
         ce = cudaEventRecord(ev[2 * k + 1], s);
         if (ce == cudaSuccess) ce = cudaStreamWaitEvent(m->copy_out, ev[2 * k + 1], 0);
         int64_t at = base;
-        for (int64_t b = k; b < n_blocks && ce == cudaSuccess; b += n_chunks) {
+        for (int64_t b = 0; b < n_blocks && ce == cudaSuccess; ++b) {
+            if (chunk_of(b) != k) continue;
             const int64_t off = b * kHostBlock, len = n - off < kHostBlock ? n - off : kHostBlock;
             ce = cudaMemcpyAsync(h_out + off, d_out + at, (size_t)len * 4, cudaMemcpyDeviceToHost, m->copy_out);
             at += len;
