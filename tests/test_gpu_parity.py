@@ -283,15 +283,15 @@ def test_host_query_and_streams(scene):
     assert torch.equal(y.cpu(), ref)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp32_simt"])
-def test_host_query_chunk_pipeline(scene, prec):
-    """Above 2^20 points the host query runs as a pipeline of chunks (copies on the model's two
-    copy streams, queries on the caller's): 4,500,001 points make four chunks with a ragged last
-    one.  Every value must equal the one-shot device query bit for bit (a point's result does
-    not depend on its batch), from pinned and from pageable host memory, on the default stream
-    and on a side stream."""
+@pytest.mark.parametrize("prec,n", [("fp32", 4500001), ("fp32_simt", 4500001), ("fp32", 1 << 20), ("fp32", (1 << 20) + 1)])
+def test_host_query_chunk_pipeline(scene, prec, n):
+    """From 2^20 points on the host query runs as a pipeline of chunks (copies on the model's two
+    copy streams, queries on the caller's) over blocks of 2^18 points: 4,500,001 points fill all
+    four chunks, with a ragged last block; 2^20 and 2^20 + 1 points leave the last chunks empty
+    (four and five blocks).  Every value must equal the one-shot device query bit for bit (a
+    point's result does not depend on its batch), from pinned and from pageable host memory, on
+    the default stream and on a side stream."""
     model, tree, m = scene
-    n = 4500001
     pts = synth.uniform_points(n, seed=43)
     ref = m.query(dev(pts), precision=prec).cpu()
     hp = torch.from_numpy(pts).pin_memory()
