@@ -24,6 +24,11 @@
  *     point with a NaN coordinate gets exit layer 0xFF, SDF NaN, gradient NaN,
  *     and sets SAND_FLAG_NAN_INPUT in the workspace flags (sand_query_stats).
  *   - n == 0 is a valid no-op.
+ *   - A model is not safe to call from several host threads at once: its default
+ *     workspace, the staging buffer and copy streams of host queries and its
+ *     packed tensor-core weights are shared by every call on it.  Callers that
+ *     share a model across threads serialise their calls, or submit through a
+ *     server (sand_server_*), which takes requests from any thread.
  */
 #ifndef SAND_H_
 #define SAND_H_
