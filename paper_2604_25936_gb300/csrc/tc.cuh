@@ -24,6 +24,9 @@ sand_status tc_prepare(TcModel *tc, const sand_tmlp_desc &d, const float *params
 // False when the driver entry point or the encoding fails.
 bool encode_u16_rows(CUtensorMap *map, const void *base, uint64_t inner, uint64_t rows, uint32_t box_inner,
                      uint32_t box_rows);
+// The same over rows of `inner` float32 elements (box_inner x 4 = 128 bytes).
+bool encode_f32_rows(CUtensorMap *map, const void *base, uint64_t inner, uint64_t rows, uint32_t box_inner,
+                     uint32_t box_rows);
 
 cudaError_t launch_tmlp_tc(const TcModel &tc, const TmlpDev &M, const float *pts, int64_t n, int full_depth, void *ws,
                            float *out, int num_sms, cudaStream_t s, int all_tails = 0, float dyn_r = 0.f,

@@ -47,6 +47,19 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
+bool encode_f32_rows(CUtensorMap *map, const void *base, uint64_t inner, uint64_t rows, uint32_t box_inner,
+                     uint32_t box_rows) {
+    auto enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t gdim[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+    cuuint64_t gstride[1] = {(cuuint64_t)inner * 4};
+    cuuint32_t box[2] = {box_inner, box_rows};
+    cuuint32_t estride[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), gdim, gstride, box, estride,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool encode_u16_rows(CUtensorMap *map, const void *base, uint64_t inner, uint64_t rows, uint32_t box_inner,
                      uint32_t box_rows) {
     auto enc = encode_fn();

@@ -48,6 +48,7 @@ constexpr int kTrThreads = 32 * 9;        // warps 5..8: epilogue
 constexpr int kTrBM = 128;                 // rows of a tile (MMA M)
 constexpr int kTrMaxStages = 4;
 constexpr int kTrSmem = 227 * 1024;
+constexpr int kTrStoreTile = 32 * 32 * 4;  // an epilogue warp's staging tile: 32 rows x 32 float32 (SW128)
 
 struct TrGemm {
     int M, N, K;          // output rows (bounds), columns (= MMA N), reduction length
@@ -68,6 +69,7 @@ struct TrGemm {
     uint32_t stage_bytes;
     // epilogue
     float *out;               // FWD: z_l [B][W]; BWD: delta'_{l-1} [B][W]; DW: partials [split][M][N]
+    int out_row0;             // row of the kernel's output tensor map holding row 0 of out
     const float *inv_s;       // device: 1 / s_l
     const float *bias;        // FWD: b_l
     const float *tw;          // FWD: tail weights of l (a at tw, b at tw + N); BWD: of l - 1
@@ -116,6 +118,19 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v) {
     asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
                  : "memory");
 }
+
+// Tensor-map store of a shared-memory tile (bulk-group completion), and the waits on it.
+__device__ __forceinline__ void tr_tma_store_2d(const CUtensorMap *map, uint32_t src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(src), "r"(x), "r"(y)
+                 : "memory");
+}
+__device__ __forceinline__ void tr_bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the source of every committed store has been read (the staging tile may be rewritten)
+__device__ __forceinline__ void tr_bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// every committed store has completed
+__device__ __forceinline__ void tr_bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Warp-uniform bounded wait: lane 0 waits, the result is broadcast (the callers go on to
 // warp-collective instructions, which every lane must reach together).
@@ -189,10 +204,13 @@ __device__ __forceinline__ void tr_produce_stage(const TrGemm &P, int pt, int m0
 //   warps 5..8  epilogue: thread (quadrant warp & 3, lane i) owns tile row 32 (warp & 3) + i
 template <int EPI>
 __global__ void __launch_bounds__(kTrThreads, 1) tr_gemm_kernel(const __grid_constant__ CUtensorMap amap,
-                                                                const __grid_constant__ CUtensorMap bmap, const TrGemm P) {
+                                                                const __grid_constant__ CUtensorMap bmap,
+                                                                const __grid_constant__ CUtensorMap omap, const TrGemm P) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)P.n_stages * P.stage_bytes);
+    // after the stage ring (1024-byte aligned): the epilogue warps' output staging tiles
+    uint8_t *stage_out = smem + (size_t)P.n_stages * P.stage_bytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stage_out + 4 * kTrStoreTile);
     uint64_t *full = bars;                       // [stage]: operands written (kTrProducers arrivals)
     uint64_t *empty = bars + kTrMaxStages;       // [stage]: the stage's MMAs completed (commit)
     uint64_t *acc_full = bars + 2 * kTrMaxStages;   // [2]: an accumulator is complete (commit)
@@ -363,6 +381,24 @@ __global__ void __launch_bounds__(kTrThreads, 1) tr_gemm_kernel(const __grid_con
         bool ok = true;
         uint32_t ti = 0;
         const float inv_s = EPI == TR_DW ? 1.f : __ldg(P.inv_s);
+        // each 32 x 32 output chunk leaves through the warp's staging tile by one TMA store: a
+        // thread writes its row's 128 bytes (swizzled, so the eight rows of a store phase hit
+        // distinct banks), instead of 32 rows' scattered float4 stores through L1
+        const uint32_t stg = smem_u32(stage_out) + (uint32_t)(q * kTrStoreTile);
+        auto put = [&](int c0, int row0, const float *o) {
+            if (lane == 0) tr_bulk_wait_read();
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                st_shared_v4(stg + tr_swz(lane, j), make_uint4(__float_as_uint(o[4 * j]), __float_as_uint(o[4 * j + 1]),
+                                                                __float_as_uint(o[4 * j + 2]), __float_as_uint(o[4 * j + 3])));
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                tr_tma_store_2d(&omap, stg, c0, row0);
+                tr_bulk_commit();
+            }
+        };
         for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++ti) {
             int m0, kb0, kb1;
             tile_kb(t, m0, kb0, kb1);
@@ -401,44 +437,37 @@ __global__ void __launch_bounds__(kTrThreads, 1) tr_gemm_kernel(const __grid_con
                     }
                 }
                 tmem_wait_ld();
+                // rows >= M: whole warps (M is a multiple of 32: the tile of a 64-wide weight gradient)
                 if (!live) continue;
+                const int orow = P.out_row0 + (EPI == TR_DW ? split * P.M : 0) + m0 + q * 32;
                 if (EPI == TR_DW) {
-                    float4 *dst = reinterpret_cast<float4 *>(P.out + ((size_t)split * P.M + row) * N + c0);
-#pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        dst[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
-                                             __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
+                    put(c0, orow, reinterpret_cast<const float *>(v));
                 } else if (EPI == TR_FWD) {
-                    float4 *dst = reinterpret_cast<float4 *>(P.out + (size_t)row * N + c0);
+                    float z[32];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        float z[4];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int col = c0 + 4 * j + e;
-                            z[e] = fmaf(__uint_as_float(v[4 * j + e]), inv_s, s_c[col]);
-                            const float h = tr_act(P.act, z[e], P.omega0);
-                            sa = fmaf(s_c[N + col], h, sa);
-                            if (P.mult) sb = fmaf(s_c[2 * N + col], h, sb);
-                        }
-                        dst[j] = make_float4(z[0], z[1], z[2], z[3]);
+                    for (int i = 0; i < 32; ++i) {
+                        const int col = c0 + i;
+                        z[i] = fmaf(__uint_as_float(v[i]), inv_s, s_c[col]);
+                        const float h = tr_act(P.act, z[i], P.omega0);
+                        sa = fmaf(s_c[N + col], h, sa);
+                        if (P.mult) sb = fmaf(s_c[2 * N + col], h, sb);
                     }
+                    put(c0, orow, z);
                 } else {  // TR_BWD
-                    float4 *dst = reinterpret_cast<float4 *>(P.out + (size_t)row * N + c0);
+                    float dd[32];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const float zv[4] = {zc[j].x, zc[j].y, zc[j].z, zc[j].w};
-                        float dd[4];
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             const int col = c0 + 4 * j + e;
                             // dt_{l-1}/dh_{l-1}: a (affine tail) or tb a + ta b (Eq. 3)
                             const float tvec = P.mult ? fmaf(tbv, s_c[N + col], tav * s_c[2 * N + col]) : s_c[N + col];
                             const float g = fmaf(__uint_as_float(v[4 * j + e]), inv_s, gl * tvec);
-                            dd[e] = g * tr_slope(P.act, zv[e], P.omega0);
+                            dd[4 * j + e] = g * tr_slope(P.act, zv[e], P.omega0);
                         }
-                        dst[j] = make_float4(dd[0], dd[1], dd[2], dd[3]);
                     }
+                    put(c0, orow, dd);
                 }
             }
             // the accumulator has been read: the MMAs of the tile after next may overwrite it
@@ -453,6 +482,8 @@ __global__ void __launch_bounds__(kTrThreads, 1) tr_gemm_kernel(const __grid_con
                 P.tb_out[row] = tb;
             }
         }
+        if (lane == 0) tr_bulk_wait_all();  // the staging tiles stay valid until every store is done
+        __syncwarp();
     }
     tc_fence_before();
     __syncthreads();
@@ -761,6 +792,9 @@ struct sand_trainer_s {
     // (l = 1..L-1), with their TMA maps (boxes of 64 x min(128, W))
     uint16_t *dt = nullptr, *ht = nullptr;
     CUtensorMap map_dt{}, map_ht{};
+    // TMA maps over the GEMM outputs, rows of W float32 in boxes of 32 x 32: Z and D ([L][cap]
+    // rows) and the weight-gradient partials ([L-1][S_dw][W] rows)
+    CUtensorMap map_z{}, map_d{}, map_dw{};
     float *Z = nullptr, *D = nullptr, *Y = nullptr, *TA = nullptr, *TB = nullptr, *G = nullptr;
     float *dw_part = nullptr, *part = nullptr, *part_bias = nullptr, *loss_part = nullptr, *loss = nullptr;
     int *mult_of = nullptr;
@@ -776,17 +810,19 @@ constexpr int kTrLossBlocks = 304;
 size_t tr_stage_bytes(int N) { return (size_t)2 * kTrBM * 128 + (size_t)2 * N * 128; }
 
 int tr_stages(int N) {
-    const size_t misc = 1024 + 8 * (3 * kTrMaxStages + 5) + 16 + (size_t)3 * N * 4;
+    const size_t misc = 1024 + 4 * kTrStoreTile + 8 * (3 * kTrMaxStages + 5) + 16 + (size_t)3 * N * 4;
     int s = (int)((kTrSmem - misc) / tr_stage_bytes(N));
     return s > kTrMaxStages ? kTrMaxStages : s;
 }
 
 size_t tr_smem(int N, int stages) {
-    return 1024 + (size_t)stages * tr_stage_bytes(N) + 8 * (3 * kTrMaxStages + 5) + 16 + (size_t)3 * N * 4;
+    return 1024 + (size_t)stages * tr_stage_bytes(N) + 4 * kTrStoreTile + 8 * (3 * kTrMaxStages + 5) + 16 +
+           (size_t)3 * N * 4;
 }
 
 template <int EPI>
-cudaError_t tr_launch(const CUtensorMap &amap, const CUtensorMap &bmap, TrGemm P, int num_sms, cudaStream_t s) {
+cudaError_t tr_launch(const CUtensorMap &amap, const CUtensorMap &bmap, const CUtensorMap &omap, TrGemm P, int num_sms,
+                      cudaStream_t s) {
     P.n_stages = tr_stages(P.N);
     P.stage_bytes = (uint32_t)tr_stage_bytes(P.N);
     const int n_tiles = P.m_tiles * P.splits;
@@ -794,7 +830,7 @@ cudaError_t tr_launch(const CUtensorMap &amap, const CUtensorMap &bmap, TrGemm P
     const size_t smem = tr_smem(P.N, P.n_stages);
     cudaError_t e = cudaFuncSetAttribute(tr_gemm_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    tr_gemm_kernel<EPI><<<grid, kTrThreads, smem, s>>>(amap, bmap, P);
+    tr_gemm_kernel<EPI><<<grid, kTrThreads, smem, s>>>(amap, bmap, omap, P);
     return cudaGetLastError();
 }
 
@@ -881,11 +917,14 @@ sand_status sand_trainer_create(sand_model m, const sand_train_opts *opts, sand_
     if (!encode_u16_rows(&T->map_f, T->wf, (uint64_t)W, (uint64_t)(L - 1) * 2 * W, 64u, (uint32_t)W) ||
         !encode_u16_rows(&T->map_b, T->wb, (uint64_t)W, (uint64_t)(L - 1) * 2 * W, 64u, (uint32_t)W) ||
         !encode_u16_rows(&T->map_dt, T->dt, (uint64_t)B, (uint64_t)(L - 1) * 2 * W, 64u, box_r) ||
-        !encode_u16_rows(&T->map_ht, T->ht, (uint64_t)B, (uint64_t)(L - 1) * 2 * W, 64u, box_r)) {
+        !encode_u16_rows(&T->map_ht, T->ht, (uint64_t)B, (uint64_t)(L - 1) * 2 * W, 64u, box_r) ||
+        !encode_f32_rows(&T->map_z, T->Z, (uint64_t)W, (uint64_t)L * B, 32u, 32u) ||
+        !encode_f32_rows(&T->map_d, T->D, (uint64_t)W, (uint64_t)L * B, 32u, 32u) ||
+        !encode_f32_rows(&T->map_dw, T->dw_part, (uint64_t)W, (uint64_t)(L - 1) * T->S_dw * W, 32u, 32u)) {
         if (prev >= 0) cudaSetDevice(prev);
         cudaFree(T->mem);
         delete T;
-        set_error("cannot encode the TMA tensor maps of the packed weights");
+        set_error("cannot encode the TMA tensor maps of the training buffers");
         return SAND_ECUDA;
     }
     std::vector<int> mult(kMaxLayers, 0);
@@ -963,6 +1002,7 @@ sand_status sand_train_step(sand_trainer T, const float *d_points, const float *
         g.a_ld = W;
         g.b_row0 = (l - 2) * 2 * W;
         g.out = Zl(l);
+        g.out_row0 = (int)((l - 1) * cap);
         g.inv_s = T->inv_scale + (l - 2);
         g.bias = P + obh + (size_t)(l - 2) * W;
         g.tw = P + otw + (size_t)(l - 1) * 2 * W;
@@ -976,7 +1016,7 @@ sand_status sand_train_step(sand_trainer T, const float *d_points, const float *
         g.m_tiles = row_tiles;
         g.splits = 1;
         g.kb_per_split = W / 64;
-        SAND_CUDA(tr_launch<TR_FWD>(T->map_f, T->map_f, g, T->num_sms, s), "forward GEMM");
+        SAND_CUDA(tr_launch<TR_FWD>(T->map_f, T->map_f, T->map_z, g, T->num_sms, s), "forward GEMM");
     }
     // loss, dL/dt (as the integers G'), delta'_L
     tr_loss_kernel<<<T->loss_blocks, 256, 0, s>>>(T->Y, d_targets, n, B, cap, L, T->G, T->loss_part);
@@ -1012,6 +1052,7 @@ sand_status sand_train_step(sand_trainer T, const float *d_points, const float *
         g.a_ld = W;
         g.b_row0 = (l - 2) * 2 * W;
         g.out = Dl(l - 1);
+        g.out_row0 = (int)((l - 2) * cap);
         g.inv_s = T->inv_scale + (l - 2);
         g.tw = P + otw + (size_t)(l - 2) * 2 * W;
         g.mult = mult && l - 1 >= 2;
@@ -1023,7 +1064,7 @@ sand_status sand_train_step(sand_trainer T, const float *d_points, const float *
         g.m_tiles = row_tiles;
         g.splits = 1;
         g.kb_per_split = W / 64;
-        SAND_CUDA(tr_launch<TR_BWD>(T->map_b, T->map_b, g, T->num_sms, s), "backward GEMM");
+        SAND_CUDA(tr_launch<TR_BWD>(T->map_b, T->map_b, T->map_d, g, T->num_sms, s), "backward GEMM");
         // delta'_{l-1}, transposed and split for the weight gradient of layer l - 1
         if (l - 1 >= 2) {
             tr_tsplit_kernel<<<dim3((unsigned)(B / 64), (unsigned)(W / 64), 1), 256, 0, s>>>(
@@ -1041,10 +1082,11 @@ sand_status sand_train_step(sand_trainer T, const float *d_points, const float *
         w.b_row0 = (l - 2) * 2 * W;
         w.box_rows = (int)(W < kTrBM ? W : kTrBM);
         w.out = T->dw_part + (size_t)(l - 2) * T->S_dw * W * W;
+        w.out_row0 = (l - 2) * T->S_dw * W;
         w.status = T->status;
         w.m_tiles = m_tiles;
         w.splits = splits;
-        SAND_CUDA(tr_launch<TR_DW>(T->map_dt, T->map_ht, w, T->num_sms, s), "weight-gradient GEMM");
+        SAND_CUDA(tr_launch<TR_DW>(T->map_dt, T->map_ht, T->map_dw, w, T->num_sms, s), "weight-gradient GEMM");
         if (splits < T->S_dw)  // unused split slots must read as zero
             SAND_CUDA(cudaMemsetAsync(w.out + (size_t)splits * W * W, 0, (size_t)(T->S_dw - splits) * W * W * 4, s),
                       "partials reset");
