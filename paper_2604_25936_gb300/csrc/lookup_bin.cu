@@ -36,6 +36,8 @@ __device__ __forceinline__ void stage_points(float *sp, const float *pts, int64_
     }
 }
 
+// COARSE: the map is a coarse table with bricks (map.coarse), else a dense finest-level grid.
+template <bool COARSE>
 __global__ void __launch_bounds__(kLookupThreads)
 lookup_kernel(MapDev map, const float *__restrict__ pts, int64_t n, int64_t per_block, int max_depth,
               float *__restrict__ out, float *__restrict__ grad, uint8_t *__restrict__ exit_ws,
@@ -56,44 +58,82 @@ lookup_kernel(MapDev map, const float *__restrict__ pts, int64_t n, int64_t per_
         __syncthreads();
         stage_points(sp, pts, c0, cn, vec != 0);
         __syncthreads();
-        for (int k = 0; k < kLookupChunk / kLookupThreads; ++k) {
+        // A thread's kPerThread points in three passes, so that the loads of one pass are all in
+        // flight together: (1) cell indices and the first map load (the dense grid's depth, or the
+        // coarse entry); (2) the brick's depth where the coarse cell is not uniform; (3) far values
+        // where the depth is 0, then the writes and the bin counts.
+        constexpr int kPerThread = kLookupChunk / kLookupThreads;
+        int dk[kPerThread];       // depth; -1 = no point, -2 = NaN coordinate
+        uint32_t ek[kPerThread];  // dense: unused; coarse: the entry's second word (uniform far value or far block)
+        uint32_t ck[kPerThread];  // dense: cell index (64-bit below); coarse: brick element index
+#pragma unroll
+        for (int k = 0; k < kPerThread; ++k) {
             const int p = k * kLookupThreads + threadIdx.x;
-            int bin = 16;  // 16 = no point
+            dk[k] = -1;
+            ek[k] = 0u;
+            ck[k] = 0u;
             if (p < cn) {
                 const float x = sp[3 * p], y = sp[3 * p + 1], z = sp[3 * p + 2];
+                if (isnan(x) || isnan(y) || isnan(z)) {
+                    dk[k] = -2;
+                } else {
+                    const int ix = cell_index(x, hr, half), iy = cell_index(y, hr, half), iz = cell_index(z, hr, half);
+                    if (!COARSE) {  // dense grid
+                        dk[k] = __ldg(map.grid + ((int64_t)iz * R + iy) * R + ix);
+                    } else {  // coarse table of cells 8 finest cells wide, then a brick
+                        const int Rc = R >> 3;
+                        const uint2 e = __ldg(map.coarse + ((int64_t)(iz >> 3) * Rc + (iy >> 3)) * Rc + (ix >> 3));
+                        const uint32_t local = (uint32_t)((((iz & 7) << 3) + (iy & 7)) * 8 + (ix & 7));
+                        ek[k] = e.y;
+                        if (e.x & 0x80000000u) {
+                            dk[k] = (int)(e.x & 0xFFu) | 0x100;  // uniform cell: bit 8 marks "far value in ek"
+                        } else {
+                            ck[k] = e.x * 512u + local;
+                            dk[k] = 0x200;  // brick load pending
+                        }
+                        if (!(e.x & 0x80000000u) && e.y != 0xFFFFFFFFu) ek[k] = e.y * 512u + local;
+                    }
+                }
+            }
+        }
+        if (COARSE) {
+#pragma unroll
+            for (int k = 0; k < kPerThread; ++k)
+                if (dk[k] == 0x200) dk[k] = 0x200 | __ldg(map.bricks + ck[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < kPerThread; ++k) {
+            const int p = k * kLookupThreads + threadIdx.x;
+            int bin = 16;  // 16 = no point
+            if (dk[k] != -1) {
                 const int64_t i = c0 + p;
                 uint8_t e;
-                if (isnan(x) || isnan(y) || isnan(z)) {
+                if (dk[k] == -2) {
                     e = kExitNaN;
                     bin = 15;
                     const float qnan = __int_as_float(0x7fc00000);
                     if (out) out[i] = qnan;
                     if (grad) grad[3 * i] = grad[3 * i + 1] = grad[3 * i + 2] = qnan;
                 } else {
-                    const int ix = cell_index(x, hr, half), iy = cell_index(y, hr, half), iz = cell_index(z, hr, half);
-                    int d;
-                    float fv = 0.0f;
-                    if (!map.coarse) {  // dense grid
-                        const int64_t c = ((int64_t)iz * R + iy) * R + ix;
-                        d = __ldg(map.grid + c);
-                        if (d == 0 && map.far) fv = __ldg(map.far + c);
-                    } else {  // coarse table of cells 8 finest cells wide, then a brick
-                        const int Rc = R >> 3;
-                        const uint2 e = __ldg(map.coarse + ((int64_t)(iz >> 3) * Rc + (iy >> 3)) * Rc + (ix >> 3));
-                        if (e.x & 0x80000000u) {
-                            d = (int)(e.x & 0xFFu);
-                            fv = __uint_as_float(e.y);
-                        } else {
-                            const int local = (((iz & 7) << 3) + (iy & 7)) * 8 + (ix & 7);
-                            d = __ldg(map.bricks + (size_t)e.x * 512 + local);
-                            if (d == 0 && e.y != 0xFFFFFFFFu) fv = __ldg(map.far_blocks + (size_t)e.y * 512 + local);
+                    int d = dk[k] & 0xFF;
+                    if (d == 0 && out) {
+                        float fv = 0.0f;
+                        if (!COARSE) {
+                            if (map.far) {
+                                const float x = sp[3 * p], y = sp[3 * p + 1], z = sp[3 * p + 2];
+                                const int ix = cell_index(x, hr, half), iy = cell_index(y, hr, half),
+                                          iz = cell_index(z, hr, half);
+                                fv = __ldg(map.far + ((int64_t)iz * R + iy) * R + ix);
+                            }
+                        } else if (dk[k] & 0x100) {
+                            fv = __uint_as_float(ek[k]);
+                        } else if (ek[k] != 0xFFFFFFFFu) {
+                            fv = __ldg(map.far_blocks + ek[k]);
                         }
+                        out[i] = fv;
                     }
                     if (d > 0 && max_depth > 0 && d > max_depth) d = max_depth;
-                    if (d == 0) {
-                        if (out) out[i] = fv;
-                        if (grad) grad[3 * i] = grad[3 * i + 1] = grad[3 * i + 2] = 0.0f;
-                    }
+                    if (d == 0 && grad) grad[3 * i] = grad[3 * i + 1] = grad[3 * i + 2] = 0.0f;
                     e = (uint8_t)d;
                     bin = d;
                 }
@@ -156,10 +196,20 @@ scatter_kernel(const float *__restrict__ pts, int64_t n, int64_t per_block, cons
         const int cn = (int)min((int64_t)kLookupChunk, end - c0);
         __syncthreads();
         stage_points(sp, pts, c0, cn, vec != 0);
-        __syncthreads();
-        for (int k = 0; k < kLookupChunk / kLookupThreads; ++k) {
+        // the exit layers of this thread's points of the chunk, loaded together with the staging
+        // (four bytes a word), not one latency per sub-chunk
+        constexpr int kPerThread = kLookupChunk / kLookupThreads;
+        uint32_t dpk[kPerThread / 4] = {};
+#pragma unroll
+        for (int k = 0; k < kPerThread; ++k) {
             const int p = k * kLookupThreads + threadIdx.x;
-            int d = (p < cn) ? exit_ws[c0 + p] : 0;
+            if (p < cn) dpk[k >> 2] |= (uint32_t)exit_ws[c0 + p] << (8 * (k & 3));
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kPerThread; ++k) {
+            const int p = k * kLookupThreads + threadIdx.x;
+            int d = (int)((dpk[k >> 2] >> (8 * (k & 3))) & 0xFFu);
             const bool net = d >= 1 && d <= L;
             const int key = net ? d : 0;
             const unsigned peers = __match_any_sync(0xffffffffu, key);
@@ -207,10 +257,10 @@ cudaError_t launch_lookup(const MapDev &map, const float *pts, int64_t n, int ma
     int64_t per;
     lookup_grid(n, &g, &per);
     const int vec = (reinterpret_cast<uintptr_t>(pts) & 15) == 0;
-    lookup_kernel<<<g, kLookupThreads, 0, s>>>(map, pts, n, per, max_depth, out, grad,
-                                               reinterpret_cast<uint8_t *>(base + L.exit), exit_layers,
-                                               reinterpret_cast<WsHeader *>(base), reinterpret_cast<uint32_t *>(base + L.hist),
-                                               g, vec, d_count);
+    auto kernel = map.coarse ? lookup_kernel<true> : lookup_kernel<false>;
+    kernel<<<g, kLookupThreads, 0, s>>>(map, pts, n, per, max_depth, out, grad, reinterpret_cast<uint8_t *>(base + L.exit),
+                                        exit_layers, reinterpret_cast<WsHeader *>(base),
+                                        reinterpret_cast<uint32_t *>(base + L.hist), g, vec, d_count);
     return cudaGetLastError();
 }
 
