@@ -185,55 +185,84 @@ scatter_kernel(const float *__restrict__ pts, int64_t n, int64_t per_block, cons
                const uint32_t *__restrict__ hist, int n_blocks, int L, float4 *__restrict__ sorted, int vec,
                const uint32_t *__restrict__ d_count) {
     if (d_count) n = min(n, (int64_t)*d_count);
+    constexpr int kPerThread = kLookupChunk / kLookupThreads;  // sub-chunks of a chunk
+    constexpr int kWarps = kLookupThreads / 32;
+    constexpr int kSeg = kPerThread * kWarps / 16;  // (sub-chunk, warp) entries per prefix thread
+    static_assert(kLookupThreads == 256 && kPerThread % 4 == 0 && kSeg * 16 == kPerThread * kWarps, "scatter layout");
     __shared__ __align__(16) float sp[kLookupChunk * 3];
-    __shared__ uint32_t base[16], wcnt[kLookupThreads / 32][16], wpre[kLookupThreads / 32][16], tot[16];
+    // per (sub-chunk k, warp w) in point order f = k * kWarps + w, per exit layer: the count, then
+    // its offset from the layer's base in this chunk (padded rows: the prefix pass reads down a
+    // column); base[c & 1][d] is layer d's next output position at the start of chunk c
+    __shared__ uint16_t pos_of[kPerThread * kWarps][17];
+    __shared__ uint32_t base[2][16];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x < 16) base[threadIdx.x] = (threadIdx.x >= 1 && threadIdx.x <= L) ? hist[threadIdx.x * n_blocks + blockIdx.x] : 0u;
+    if (threadIdx.x < 16)
+        base[0][threadIdx.x] = (threadIdx.x >= 1 && threadIdx.x <= L) ? hist[threadIdx.x * n_blocks + blockIdx.x] : 0u;
+    int par = 0;
     const int64_t start = (int64_t)blockIdx.x * per_block;
     const int64_t end = min(n, start + per_block);
     const unsigned lt_mask = (1u << lane) - 1u;
     for (int64_t c0 = start; c0 < end; c0 += kLookupChunk) {
         const int cn = (int)min((int64_t)kLookupChunk, end - c0);
-        __syncthreads();
+        __syncthreads();  // the previous chunk is written out
         stage_points(sp, pts, c0, cn, vec != 0);
         // the exit layers of this thread's points of the chunk, loaded together with the staging
         // (four bytes a word), not one latency per sub-chunk
-        constexpr int kPerThread = kLookupChunk / kLookupThreads;
         uint32_t dpk[kPerThread / 4] = {};
 #pragma unroll
         for (int k = 0; k < kPerThread; ++k) {
             const int p = k * kLookupThreads + threadIdx.x;
             if (p < cn) dpk[k >> 2] |= (uint32_t)exit_ws[c0 + p] << (8 * (k & 3));
         }
+        for (int i = threadIdx.x; i < kPerThread * kWarps * 17; i += kLookupThreads) (&pos_of[0][0])[i] = 0;
         __syncthreads();
+        // (1) every warp counts each exit layer in each sub-chunk
+#pragma unroll
+        for (int k = 0; k < kPerThread; ++k) {
+            const int d = (int)((dpk[k >> 2] >> (8 * (k & 3))) & 0xFFu);
+            const bool net = d >= 1 && d <= L;
+            const unsigned peers = __match_any_sync(0xffffffffu, net ? d : 0);
+            if (net && (peers & lt_mask) == 0u) pos_of[k * kWarps + warp][d] = (uint16_t)__popc(peers);
+        }
+        __syncthreads();
+        // (2) per exit layer b, sixteen threads turn the counts into offsets: each sums kSeg
+        // consecutive entries, a 16-lane shuffle scan gives the exclusive prefix, the base moves on
+        {
+            const int b = threadIdx.x >> 4, j = threadIdx.x & 15;
+            uint32_t v[kSeg], sum = 0;
+#pragma unroll
+            for (int i = 0; i < kSeg; ++i) {
+                v[i] = pos_of[kSeg * j + i][b];
+                sum += v[i];
+            }
+            uint32_t incl = sum;
+#pragma unroll
+            for (int o = 1; o < 16; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o, 16);
+                if (j >= o) incl += t;
+            }
+            uint32_t run = incl - sum;
+#pragma unroll
+            for (int i = 0; i < kSeg; ++i) {
+                pos_of[kSeg * j + i][b] = (uint16_t)run;
+                run += v[i];
+            }
+            if (j == 15) base[par ^ 1][b] = base[par][b] + run;
+        }
+        __syncthreads();
+        // (3) every network point to its position: the sub-chunk's and warp's start plus its rank
 #pragma unroll
         for (int k = 0; k < kPerThread; ++k) {
             const int p = k * kLookupThreads + threadIdx.x;
-            int d = (int)((dpk[k >> 2] >> (8 * (k & 3))) & 0xFFu);
+            const int d = (int)((dpk[k >> 2] >> (8 * (k & 3))) & 0xFFu);
             const bool net = d >= 1 && d <= L;
-            const int key = net ? d : 0;
-            const unsigned peers = __match_any_sync(0xffffffffu, key);
-            const int rank = __popc(peers & lt_mask);
-            if (threadIdx.x < 16 * (kLookupThreads / 32)) (&wcnt[0][0])[threadIdx.x] = 0u;
-            __syncthreads();
-            if (net && rank == 0) wcnt[warp][d] = (uint32_t)__popc(peers);
-            __syncthreads();
-            if (threadIdx.x < 16) {
-                uint32_t acc = 0;
-                for (int w = 0; w < kLookupThreads / 32; ++w) {
-                    wpre[w][threadIdx.x] = acc;
-                    acc += wcnt[w][threadIdx.x];
-                }
-                tot[threadIdx.x] = acc;
-            }
-            __syncthreads();
+            const unsigned peers = __match_any_sync(0xffffffffu, net ? d : 0);
             if (net) {
-                const uint32_t pos = base[d] + wpre[warp][d] + (uint32_t)rank;
+                const uint32_t pos = base[par][d] + pos_of[k * kWarps + warp][d] + (uint32_t)__popc(peers & lt_mask);
                 sorted[pos] = make_float4(sp[3 * p], sp[3 * p + 1], sp[3 * p + 2], __int_as_float((int)(c0 + p)));
             }
-            __syncthreads();
-            if (threadIdx.x < 16) base[threadIdx.x] += tot[threadIdx.x];
         }
+        par ^= 1;
     }
 }
 
