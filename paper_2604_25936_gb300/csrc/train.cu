@@ -13,6 +13,8 @@
 //   tr_loss            per row: G'_k = sum_{i>=k} sign(y_i - y_gt) (an integer; dL/dt_k = G'_k / n)
 //                      and |y_i - y_gt| summed per block;
 //   tr_top             delta'_L = G'_L dt_L/dh_L * act'(z_L)   (delta' = n dL/dz);
+//   tr_tsplit          act(z_l)^T (l = 1..L-1) and each delta'_l^T, transposed and split into
+//                      fp16 hi + lo: the weight gradient's operands, K (the batch) contiguous;
 //   tr_gemm<BWD>       l = L..2: delta'_{l-1} = (delta'_l W_l + G'_{l-1} dt_{l-1}/dh_{l-1}) * act'(z_{l-1});
 //   tr_gemm<DW>        l = 2..L: partial sums over row ranges of delta'_l^T act(Z_{l-1}), split over
 //                      the CTAs along the rows (the reduction dimension);
@@ -22,10 +24,12 @@
 //                      parameter-block order;
 //   tr_adam            one Adam update of the float32 master parameters.
 // Every value stays float32 in memory; activations are recomputed from the stored z where an
-// operand needs them.  Tensor-core operands are split on the fly by the producer warps of the
-// GEMM (a = hi + lo, fp16 each; D = A_hi B_hi + A_lo B_hi + A_hi B_lo), written into shared
-// memory in the 128-byte swizzled K-major layout, and multiplied by tcgen05.mma (kind::f16,
-// M = 128, N = W, fp32 accumulator in TMEM).  delta' = n dL/dz keeps the backward operands away
+// operand needs them.  Each product is D = A_hi B_hi + A_lo B_hi + A_hi B_lo (a = hi + lo, fp16
+// each) by tcgen05.mma (kind::f16, M = 128, N = W, fp32 accumulator in TMEM) from shared memory
+// in the 128-byte swizzled K-major layout.  The forward and backward A operands are split on the
+// fly by the GEMM's producer warps; the packed weights and the weight gradient's operands are
+// split beforehand and arrive by TMA.  The epilogue sends each 32 x 32 block of its output out
+// by a TMA store from a shared-memory staging tile.  delta' = n dL/dz keeps the backward operands away
 // from the fp16 subnormals; 1/n is applied once, at the end.
 #include <math.h>
 #include <string.h>
